@@ -1,0 +1,66 @@
+"""Arnoldi function approximation f(A)x ~ beta V_k f(H_k) e_1.
+
+Arnoldi recurrence A V_k = V_k H_k + beta_k v_(k+1) e_k^T with v_1 = x/beta,
+beta = |x| (Sec. 4, Eq. Arnoldi); H_k = V_k^dagger A V_k (Eq. HVAV); the
+approximation beta V_k f(H_k) e_1 (Eq. yproj3). With f = sgn, f(H_k) comes
+from Roberts' iteration (Sec. 5.2, Eq. Roberts).
+
+Readings where the paper is silent:
+
+* orthogonalisation: classical Gram-Schmidt applied twice (CGS2) per step:
+  h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2, column = h1 + h2;
+* breakdown: if H_(j+1,j) <= 1e-14 ||H_(1:j+1,1:j)||_F the Krylov space is
+  invariant, the recurrence stops and k_used = j (the result is then exact).
+"""
+
+import numpy as np
+
+from .newton import roberts_sign
+
+BREAKDOWN_TOL = 1e-14
+
+
+def arnoldi(matvec, x, k):
+    """Run k Arnoldi steps on x.
+
+    Returns (V, H, beta, k_used): V is N x (k_used+1) (the last column is
+    v_(k_used+1), zero after a breakdown), H is (k_used+1) x k_used.
+    """
+    x = np.asarray(x, dtype=np.complex128)
+    n = x.shape[0]
+    beta = np.linalg.norm(x)
+    v = np.zeros((n, k + 1), dtype=np.complex128)
+    h = np.zeros((k + 1, k), dtype=np.complex128)
+    if beta == 0.0 or k == 0:
+        return v[:, :1], h[:1, :0], beta, 0
+    v[:, 0] = x / beta
+    for j in range(k):
+        w = matvec(v[:, j])
+        basis = v[:, : j + 1]
+        h1 = basis.conj().T @ w
+        w = w - basis @ h1
+        h2 = basis.conj().T @ w
+        w = w - basis @ h2
+        h[: j + 1, j] = h1 + h2
+        hn = np.linalg.norm(w)
+        h[j + 1, j] = hn
+        if hn <= BREAKDOWN_TOL * np.linalg.norm(h[: j + 2, : j + 1]):
+            h[j + 1, j] = 0.0
+            return v[:, : j + 2] * np.r_[np.ones(j + 1), 0.0], h[: j + 2, : j + 1], beta, j + 1
+        v[:, j + 1] = w / hn
+    return v, h, beta, k
+
+
+def arnoldi_sign(matvec, x, k, **newton_kw):
+    """beta V_k sgn(H_k) e_1 (Eq. yproj3 with f = sgn).
+
+    Returns (y, info) with info = dict(k_used, beta, newton_iters, coeff).
+    """
+    v, h, beta, k_used = arnoldi(matvec, x, k)
+    if k_used == 0:
+        return np.zeros_like(np.asarray(x, dtype=np.complex128)), dict(
+            k_used=0, beta=beta, newton_iters=0, coeff=np.zeros(0, np.complex128))
+    s, it = roberts_sign(h[:k_used, :k_used], **newton_kw)
+    coeff = beta * s[:, 0]
+    y = v[:, :k_used] @ coeff
+    return y, dict(k_used=k_used, beta=beta, newton_iters=it, coeff=coeff, H=h)
