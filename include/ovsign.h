@@ -1,0 +1,193 @@
+/*
+ * ovsign.h -- C ABI of a GB300 (sm_103a) library that computes
+ *
+ *     y = sgn(H_w(mu)) x,      H_w(mu) = gamma5 D_w(mu),
+ *
+ * for the Wilson-Dirac operator at quark chemical potential mu, by the
+ * deflated Arnoldi method of Bloch, Frommer, Lang and Wettig (2007):
+ * LR deflation of critical eigenvectors (Sec. 5.3, Eq. fAxLRArn), an
+ * Arnoldi basis of the deflated Krylov space (Sec. 4, Eq. Arnoldi) and the
+ * sign of the small Hessenberg matrix by Roberts' Newton iteration
+ * (Sec. 5.2, Eq. Roberts).
+ *
+ * Conventions used throughout
+ * ---------------------------
+ *  - dims = {Lx, Ly, Lz, Lt}; V = Lx Ly Lz Lt sites; N = 12 V unknowns.
+ *    Site s = ((t*Lz + z)*Ly + y)*Lx + x. Direction nu = 0,1,2,3 is x,y,z,t.
+ *    Every extent must be >= 2. Boundaries: periodic in space, antiperiodic
+ *    in time.
+ *  - Vectors are complex128, interleaved (re, im), entry
+ *    (s*4 + spin)*3 + colour; nrhs vectors are stored one after another
+ *    ([nrhs][N]). Spin basis: chiral, gamma5 = diag(1, 1, -1, -1).
+ *  - Links are complex128 [V][4][3][3] (row, column); U_nu(s) joins s to
+ *    s + nu-hat.
+ *  - D_w(mu) x(s) = x(s) - kappa sum_nu [ (1 - gamma_nu) e^{+mu d_nu3}
+ *    U_nu(s) x(s+nu) + (1 + gamma_nu) e^{-mu d_nu3} U_nu(s-nu)^+ x(s-nu) ],
+ *    kappa = 1/(8 + 2 m_w)  (Sec. 2, Eq. Dw, with the projectors in the
+ *    order (1 - gamma) forward, which is gamma5-conjugate to the printed
+ *    order and has the same spectrum).
+ *  - Pointers to vectors may be device or host memory; the library asks the
+ *    CUDA runtime which. Host buffers are staged through device memory with
+ *    copies on the given stream. All device work is enqueued on `stream`
+ *    (a cudaStream_t; NULL means the legacy default stream).
+ *  - Every entry point returns an ovs_status; no C++ exception crosses
+ *    the ABI. On error ovs_last_error() returns a message (thread local).
+ *  - A handle is not thread safe: use one handle per host thread. The
+ *    library owns the device memory behind a handle (links, deflation
+ *    basis, Krylov workspaces, grown on demand with cudaMalloc) until
+ *    ovs_destroy.
+ */
+#ifndef OVSIGN_H
+#define OVSIGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ovs_gauge_s* ovs_gauge_t;
+
+typedef enum {
+    OVS_OK = 0,
+    OVS_NOT_CONVERGED = 1, /* result usable but flagged (see ovs_apply_info) */
+    OVS_EINVAL = -1,       /* bad argument */
+    OVS_ENOMEM = -2,       /* device or host allocation failed */
+    OVS_ECUDA = -3,        /* CUDA runtime or library error */
+    OVS_ESTATE = -4,       /* mu not set, or deflation required but absent */
+    OVS_EEIG = -5,         /* eigensolver did not converge */
+    OVS_ESIGN = -6,        /* sign undefined: eigenvalue on the imaginary axis */
+    OVS_ETIMEOUT = -7,     /* a bounded device wait gave up */
+    OVS_EIO = -8           /* file read/write failed or bad file */
+} ovs_status;
+
+/* Arithmetic of the path. OVS_F64: links, vectors and Krylov basis in
+ * complex128. OVS_MIXED: links, matvec and Krylov basis in complex64 with
+ * FP64 accumulation of Gram-Schmidt inner products, FP64 Hessenberg
+ * entries, FP64 deflation coefficients and FP64 Newton sign; input and
+ * output vectors stay complex128. */
+enum { OVS_F64 = 0, OVS_MIXED = 1 };
+
+/* Operators for ovs_matvec. */
+enum { OVS_OP_DW = 0, OVS_OP_HW = 1, OVS_OP_HW2 = 2 };
+
+/* Create a handle on the current CUDA device with a seeded SU(3) field:
+ * per link l = 4 s + nu, eighteen normals from Philox4x32-10 (counter
+ * (l mod 2^32, l div 2^32, j, 0), j = 0..8, key = seed) by Box-Muller,
+ * A = normals as a complex 3x3, X = traceless Hermitian part of A,
+ * U = exp(i eps X) (Taylor series with scaling and squaring), reunitarised
+ * to SU(3). This is the synthetic stand-in for the paper's gauge ensembles
+ * (Sec. 6). prec: OVS_F64 or OVS_MIXED (which precisions the handle keeps
+ * on the device; OVS_MIXED keeps both). Errors: EINVAL (dims < 2, eps < 0,
+ * bad prec), ENOMEM, ECUDA. */
+int ovs_create_gauge(const int32_t dims[4], uint64_t seed, double eps, int32_t prec,
+                     ovs_gauge_t* out);
+
+/* Create a handle from caller links (host, complex128 [V][4][3][3]). The
+ * library copies them; the caller keeps ownership of `links`. The links
+ * need not be unitary. Errors: as ovs_create_gauge. */
+int ovs_create_gauge_from_links(const int32_t dims[4], const double* links, int32_t prec,
+                                ovs_gauge_t* out);
+
+/* Copy the handle's complex128 links back to host `links_out`
+ * ([V][4][3][3], 72 V doubles). Synchronises the device. */
+int ovs_get_links(ovs_gauge_t g, double* links_out);
+
+/* Set mu and the Wilson mass m_w (kappa = 1/(8 + 2 m_w), Sec. 2). The paper
+ * takes m_w in (-2, 0); any m_w with 8 + 2 m_w != 0 is accepted. Clears any
+ * deflation basis (it belongs to the old operator). Host only. */
+int ovs_set_mu(ovs_gauge_t g, double mu, double m_w);
+
+/* y = op x for nrhs vectors, op = OVS_OP_DW (D_w(mu)), OVS_OP_HW (H_w(mu)),
+ * OVS_OP_HW2 (H_w(mu)^2, used to find the critical eigenvalues, Sec. 6).
+ * prec selects the arithmetic (OVS_F64 or OVS_MIXED); x and y are
+ * complex128 either way. x and y must not overlap. Errors: EINVAL, ESTATE
+ * (mu not set), ECUDA. */
+int ovs_matvec(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, int32_t prec,
+               void* stream);
+
+/* Compute the m critical eigenpairs of H_w(mu) on the GPU for LR deflation
+ * (Sec. 5.3 step i, Sec. 6): eigenvalues of smallest |lambda| found through
+ * H_w(mu)^2 (the paper's choice), right vectors R with H R = R Lambda, left
+ * vectors as right eigenvectors of H_w(mu)^+ = H_w(-mu) (gamma5-
+ * hermiticity), biorthonormalised so that L^+ R = I. The m kept are those
+ * of smallest |Re lambda| among the converged ones. tol: relative residual
+ * ||H r - lambda r|| / ||H|| asked of each pair (e.g. 1e-10). eig_out, if
+ * not NULL, receives the m eigenvalues as 2m doubles (re, im), sorted by
+ * |Re lambda|. Synchronises the device. Errors: EINVAL, ESTATE, EEIG (the
+ * pairs did not reach tol within the iteration budget; the basis is still
+ * installed and eig_out filled), ENOMEM, ECUDA. */
+int ovs_deflate_setup(ovs_gauge_t g, int32_t m, double tol, double* eig_out);
+
+/* Install a deflation basis given by the caller (host complex128 arrays
+ * R and L of [m][N], lambda of 2m doubles). L is biorthonormalised against
+ * R (L <- L (L^+ R)^-+). m = 0 removes deflation. Errors: EINVAL, ESTATE
+ * (mu not set), ESIGN (some Re lambda == 0), ENOMEM, ECUDA. */
+int ovs_deflate_load(ovs_gauge_t g, int32_t m, const double* R, const double* L,
+                     const double* lambda);
+
+/* Copy the installed basis to host buffers (any may be NULL):
+ * R, L: [m][N] complex128 (L biorthonormalised), lambda: 2m doubles.
+ * m_out receives m. Synchronises the device. */
+int ovs_deflate_get(ovs_gauge_t g, int32_t* m_out, double* R, double* L, double* lambda);
+
+/* Save / restore the deflation basis to a binary file (header with dims,
+ * mu, m_w, m and a checksum, then lambda, R, L in complex128). Restore
+ * checks that dims, mu and m_w match the handle. Errors: EIO, ESTATE. */
+int ovs_deflate_save(ovs_gauge_t g, const char* path);
+int ovs_deflate_restore(ovs_gauge_t g, const char* path);
+
+/* Options of a sign application. */
+typedef struct {
+    int32_t k_max;       /* Krylov dimension (Sec. 4 suggests even values) */
+    int32_t check_every; /* 0: run exactly k_max steps (stop only at breakdown);
+                            >0 (even): every check_every steps estimate the
+                            error from successive coefficient vectors and
+                            stop a right-hand side once it is below tol */
+    int32_t prec;        /* OVS_F64 or OVS_MIXED */
+    int32_t reserved;    /* must be 0 */
+    double tol;          /* tolerance for check_every > 0 */
+} ovs_apply_opts;
+
+/* Per right-hand-side report. */
+typedef struct {
+    int32_t k_used;       /* Krylov dimension used (< k_max after breakdown) */
+    int32_t newton_iters; /* Roberts iterations on H_k */
+    int32_t status;       /* OVS_OK, OVS_NOT_CONVERGED or OVS_ESIGN */
+    int32_t reserved;
+    double beta;          /* ||x_ominus||, the norm of the deflated source */
+    double est_err;       /* last error estimate (check_every > 0), else 0 */
+} ovs_apply_info;
+
+/* y = sgn(H_w(mu)) x for nrhs vectors (Sec. 5.3, Eq. fAxLRArn):
+ *   c = L^+ x, x_ominus = x - R c, y = R sgn(Re Lambda) c
+ *     + beta V_k sgn(H_k) e_1 with the Arnoldi basis V_k of
+ *   K_k(H_w, x_ominus), beta = ||x_ominus||; without a deflation basis the
+ *   first three terms vanish (Sec. 4, Eq. yproj3).
+ * Each right-hand side has its own Krylov basis; all are advanced together.
+ * x: input [nrhs][N], y: output [nrhs][N] (complex128, host or device, must
+ * not overlap). If info is not NULL the call waits for the stream and fills
+ * nrhs reports; if NULL the call returns once the work is enqueued and
+ * ovs_get_info() reads the reports later. Returns the worst per-RHS status
+ * when info is given. Errors: EINVAL, ESTATE (mu not set), ENOMEM, ECUDA. */
+int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
+                   ovs_apply_info* info, void* stream);
+
+/* Reports of the last ovs_sign_apply on this handle (waits for its stream). */
+int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs);
+
+/* Thread-local message of the last error (never NULL). */
+const char* ovs_last_error(void);
+
+/* Library version string. */
+const char* ovs_version(void);
+
+/* Release the handle and all device memory it owns. NULL is ignored. */
+void ovs_destroy(ovs_gauge_t g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OVSIGN_H */

@@ -9,7 +9,7 @@ Readings where the paper is silent:
 
 * orthogonalisation: classical Gram-Schmidt applied twice (CGS2) per step:
   h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2, column = h1 + h2;
-* breakdown: if H_(j+1,j) <= 1e-14 ||H_(1:j+1,1:j)||_F the Krylov space is
+* breakdown: if H_(j+1,j) <= 1e-12 ||H_(1:j+1,1:j)||_F the Krylov space is
   invariant, the recurrence stops and k_used = j (the result is then exact).
 """
 
@@ -17,7 +17,7 @@ import numpy as np
 
 from .newton import roberts_sign
 
-BREAKDOWN_TOL = 1e-14
+BREAKDOWN_TOL = 1e-12
 
 
 def arnoldi(matvec, x, k):

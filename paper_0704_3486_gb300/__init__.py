@@ -1,0 +1,249 @@
+"""Python binding of libovsign (include/ovsign.h): sgn(H_w(mu)) x on GB300.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Vectors are torch tensors of dtype complex128 with shape
+[nrhs, N] (N = 12 V, entry (site*4 + spin)*3 + colour), on the GPU or on
+the host (the library stages host buffers itself). Functions mirror the C
+entry points without the ``ovs_`` prefix and raise ``OvsError`` on a
+negative status.
+
+There is no CPU fallback: ``load()`` raises if the shared library is
+missing, and the library needs a CUDA device to do any work.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libovsign.so")
+
+F64 = 0
+MIXED = 1
+OP_DW, OP_HW, OP_HW2 = 0, 1, 2
+STATUS = {
+    0: "OVS_OK", 1: "OVS_NOT_CONVERGED", -1: "OVS_EINVAL", -2: "OVS_ENOMEM", -3: "OVS_ECUDA",
+    -4: "OVS_ESTATE", -5: "OVS_EEIG", -6: "OVS_ESIGN", -7: "OVS_ETIMEOUT", -8: "OVS_EIO",
+}
+EXPORTS = [
+    "ovs_create_gauge", "ovs_create_gauge_from_links", "ovs_get_links", "ovs_set_mu", "ovs_matvec",
+    "ovs_deflate_setup", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
+    "ovs_sign_apply", "ovs_get_info", "ovs_last_error", "ovs_version", "ovs_destroy",
+]
+
+
+class OvsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ApplyOpts(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int32), ("check_every", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class ApplyInfo(ctypes.Structure):
+    _fields_ = [("k_used", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("beta", ctypes.c_double), ("est_err", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"k_used": self.k_used, "newton_iters": self.newton_iters, "status": self.status,
+                "beta": self.beta, "est_err": self.est_err}
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with paper_0704_3486_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    p_i32 = ctypes.POINTER(ctypes.c_int32)
+    p_dbl = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "ovs_create_gauge": ([p_i32, ctypes.c_uint64, dbl, i32, ctypes.POINTER(vp)], i32),
+        "ovs_create_gauge_from_links": ([p_i32, vp, i32, ctypes.POINTER(vp)], i32),
+        "ovs_get_links": ([vp, vp], i32),
+        "ovs_set_mu": ([vp, dbl, dbl], i32),
+        "ovs_matvec": ([vp, i32, vp, vp, i32, i32, vp], i32),
+        "ovs_deflate_setup": ([vp, i32, dbl, vp], i32),
+        "ovs_deflate_load": ([vp, i32, vp, vp, vp], i32),
+        "ovs_deflate_get": ([vp, p_i32, vp, vp, vp], i32),
+        "ovs_deflate_save": ([vp, ctypes.c_char_p], i32),
+        "ovs_deflate_restore": ([vp, ctypes.c_char_p], i32),
+        "ovs_sign_apply": ([vp, vp, vp, i32, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp], i32),
+        "ovs_get_info": ([vp, ctypes.POINTER(ApplyInfo), i32], i32),
+        "ovs_last_error": ([], ctypes.c_char_p),
+        "ovs_version": ([], ctypes.c_char_p),
+        "ovs_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    del p_dbl
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status < 0:
+        raise OvsError(status, _lib.ovs_last_error().decode())
+    return status
+
+
+def _dims(dims):
+    return (ctypes.c_int32 * 4)(*[int(d) for d in dims])
+
+
+def _ptr(t):
+    """Data pointer of a contiguous complex128 tensor or numpy array."""
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if not t.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C contiguous")
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:  # pragma: no cover
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Gauge:
+    """Owns an ``ovs_gauge_t`` handle (released by ``destroy`` or GC)."""
+
+    def __init__(self, handle, dims):
+        self.handle = handle
+        self.dims = tuple(int(d) for d in dims)
+        self.V = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        self.N = 12 * self.V
+
+    def destroy(self):
+        if self.handle:
+            load().ovs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def create_gauge(dims, seed, eps, prec=MIXED):
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.ovs_create_gauge(_dims(dims), ctypes.c_uint64(int(seed)), float(eps), int(prec), ctypes.byref(h)))
+    return Gauge(h, dims)
+
+
+def create_gauge_from_links(dims, links, prec=MIXED):
+    """links: complex128 array [V][4][3][3] (numpy or CPU tensor)."""
+    import numpy as np
+    lib = load()
+    arr = np.ascontiguousarray(np.asarray(links, dtype=np.complex128))
+    h = ctypes.c_void_p()
+    _check(lib.ovs_create_gauge_from_links(_dims(dims), _ptr(arr), int(prec), ctypes.byref(h)))
+    return Gauge(h, dims)
+
+
+def get_links(g):
+    import numpy as np
+    out = np.empty((g.V, 4, 3, 3), dtype=np.complex128)
+    _check(load().ovs_get_links(g.handle, _ptr(out)))
+    return out
+
+
+def set_mu(g, mu, m_w):
+    _check(load().ovs_set_mu(g.handle, float(mu), float(m_w)))
+
+
+def matvec(g, op, x, y, nrhs=None, prec=F64, stream=None):
+    nrhs = x.shape[0] if nrhs is None else nrhs
+    _check(load().ovs_matvec(g.handle, int(op), _ptr(x), _ptr(y), int(nrhs), int(prec), _stream(stream)))
+
+
+def deflate_setup(g, m, tol=1e-10):
+    import numpy as np
+    eig = np.empty(2 * m, dtype=np.float64)
+    status = load().ovs_deflate_setup(g.handle, int(m), float(tol), _ptr(eig))
+    _check(status)
+    return eig[0::2] + 1j * eig[1::2], status
+
+
+def deflate_load(g, R, L, lam):
+    """R, L: complex128 [m][N] (host); lam: m complex eigenvalues."""
+    import numpy as np
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.complex128))
+    L = np.ascontiguousarray(np.asarray(L, dtype=np.complex128))
+    lam = np.asarray(lam, dtype=np.complex128)
+    lam2 = np.ascontiguousarray(np.stack([lam.real, lam.imag], axis=-1).reshape(-1))
+    m = lam.shape[0]
+    if m == 0:
+        _check(load().ovs_deflate_load(g.handle, 0, None, None, None))
+        return
+    _check(load().ovs_deflate_load(g.handle, int(m), _ptr(R), _ptr(L), _ptr(lam2)))
+
+
+def deflate_get(g):
+    import numpy as np
+    m = ctypes.c_int32()
+    lib = load()
+    _check(lib.ovs_deflate_get(g.handle, ctypes.byref(m), None, None, None))
+    m = m.value
+    R = np.empty((m, g.N), dtype=np.complex128)
+    L = np.empty((m, g.N), dtype=np.complex128)
+    lam = np.empty(2 * m, dtype=np.float64)
+    if m:
+        _check(lib.ovs_deflate_get(g.handle, None, _ptr(R), _ptr(L), _ptr(lam)))
+    return R, L, lam[0::2] + 1j * lam[1::2]
+
+
+def deflate_save(g, path):
+    _check(load().ovs_deflate_save(g.handle, os.fsencode(path)))
+
+
+def deflate_restore(g, path):
+    _check(load().ovs_deflate_restore(g.handle, os.fsencode(path)))
+
+
+def sign_apply(g, x, y, k_max, prec=MIXED, nrhs=None, check_every=0, tol=0.0, stream=None, want_info=True):
+    """y = sgn(H_w(mu)) x. Returns (status, [info dicts]) if want_info, else status."""
+    nrhs = x.shape[0] if nrhs is None else nrhs
+    opts = ApplyOpts(int(k_max), int(check_every), int(prec), 0, float(tol))
+    lib = load()
+    if want_info:
+        info = (ApplyInfo * nrhs)()
+        st = _check(lib.ovs_sign_apply(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), info,
+                                       _stream(stream)))
+        return st, [i.as_dict() for i in info]
+    return _check(lib.ovs_sign_apply(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), None,
+                                     _stream(stream)))
+
+
+def get_info(g, nrhs):
+    info = (ApplyInfo * nrhs)()
+    st = _check(load().ovs_get_info(g.handle, info, int(nrhs)))
+    return st, [i.as_dict() for i in info]
+
+
+def version():
+    return load().ovs_version().decode()

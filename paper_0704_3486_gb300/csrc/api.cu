@@ -1,0 +1,735 @@
+// C ABI (include/ovsign.h): handles, operator set-up, deflation basis and
+// the sign application
+//
+//   y = R sgn(Lambda) L^+ x + beta V_k sgn(H_k) e_1,  x_ominus = x - R L^+ x
+//
+// (Sec. 5.3, Eqs. xdec, fARLx, LRArnoldi, fAxLRArn; Sec. 4, Eq. yproj3),
+// enqueued on the caller's stream as a sequence of kernels:
+// K7 layout -> K5 projection -> norm -> k x (K1 matvec, K2 CGS2 sweeps)
+// -> K3 Newton sign of H_k -> K4 recombination -> K7 layout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ovsign.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ovs {
+void generate_links(long long V, uint64_t seed, double eps, double* links);
+int eig_setup(struct ovs_gauge_s* g, int m, double tol, double* eig_out);
+}  // namespace ovs
+
+using namespace ovs;
+
+// --------------------------------------------------------------- errors
+static thread_local std::string g_err = "no error";
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            if (e_ == cudaErrorMemoryAllocation)                                                      \
+                return fail(OVS_ENOMEM, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return fail(OVS_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+        }                                                                                             \
+    } while (0)
+
+#define TRY(call)                 \
+    do {                          \
+        int s_ = (call);          \
+        if (s_ < 0) return s_;    \
+    } while (0)
+
+// --------------------------------------------------------------- handle
+template <typename T> static cudaError_t dalloc(T** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    return cudaMalloc((void**)p, bytes);
+}
+template <typename T> static void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+struct VecWork {  // per-right-hand-side vectors
+    int nrhs = 0, prec = -1;
+    void* xint = nullptr;  // [nrhs][N] precision prec (x, then x_ominus)
+    void* wvec = nullptr;  // [nrhs][N] precision prec (Arnoldi w)
+    void* yacc = nullptr;  // [nrhs][N] complex128 internal (y accumulator)
+    void* sx = nullptr;    // [nrhs][N] complex128 canonical staging (host x)
+    void* sy = nullptr;    // [nrhs][N] complex128 canonical staging (host y)
+};
+
+struct KryWork {  // Krylov basis and small matrices
+    int nrhs = 0, kmax = 0, prec = -1, jcap = 0, nblk = 0;
+    void* basis = nullptr;       // [nrhs][kmax+1][N] precision prec
+    void* H = nullptr;           // [nrhs][(kmax+1) x kmax] complex128, column-major
+    void* htmp = nullptr;        // [nrhs][jcap] complex128
+    void* partial = nullptr;     // [nrhs][nblk][jcap] complex128
+    double* norm_part = nullptr; // [nrhs][nblk]
+    double* beta = nullptr;
+    double* inv_beta = nullptr;
+    double* hnorm2 = nullptr;
+    int* active = nullptr;
+    int* k_used = nullptr;
+    int* iters = nullptr;
+    int* status = nullptr;
+    void* coeff = nullptr;  // [nrhs][kmax] complex128
+    void* newton = nullptr; // [nrhs][2 kmax^2] complex128
+    void* cdef = nullptr;   // [nrhs][m] complex128 deflation coefficients
+    void* cdef2 = nullptr;  // [nrhs][m] complex128 sgn-scaled
+};
+
+struct ovs_gauge_s {
+    int dims[4];
+    Geom geom;
+    long long V = 0, N = 0;
+    int prec = OVS_F64;
+    int device = 0, num_sms = 148;
+    bool mu_set = false;
+    double mu = 0.0, m_w = 0.0, kappa = 0.0;
+    void* links64 = nullptr;  // [4][9][V] double2
+    void* links32 = nullptr;  // [4][9][V] float2 (OVS_MIXED)
+    // deflation basis (internal layout)
+    int m = 0;
+    void* R64 = nullptr;  // [m][N] double2 planes
+    void* L64 = nullptr;  // biorthonormalised
+    void* R32 = nullptr;  // [m][N/2] float4 planes
+    void* L32 = nullptr;
+    double* sgn = nullptr;  // device [m]
+    std::vector<double> lambda;  // host 2m
+    VecWork vw;
+    KryWork kw;
+    int last_nrhs = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+// helpers exposed to other translation units of the library
+namespace ovs {
+int lib_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace ovs
+
+static size_t field_bytes(long long N, int tprec) { return (size_t)N * (tprec == PREC_F64 ? 16 : 8); }
+static long long field_units(long long N, int tprec) { return tprec == PREC_F64 ? N : N / 2; }
+static int tprec_of(int prec) { return prec == OVS_MIXED ? PREC_F32 : PREC_F64; }
+static const void* links_for(const ovs_gauge_s* g, int tprec) { return tprec == PREC_F64 ? g->links64 : g->links32; }
+
+static void free_vec(VecWork& w) {
+    dfree(w.xint);
+    dfree(w.wvec);
+    dfree(w.yacc);
+    dfree(w.sx);
+    dfree(w.sy);
+    w.nrhs = 0;
+    w.prec = -1;
+}
+
+static void free_kry(KryWork& k) {
+    dfree(k.basis);
+    dfree(k.H);
+    dfree(k.htmp);
+    dfree(k.partial);
+    dfree(k.norm_part);
+    dfree(k.beta);
+    dfree(k.inv_beta);
+    dfree(k.hnorm2);
+    dfree(k.active);
+    dfree(k.k_used);
+    dfree(k.iters);
+    dfree(k.status);
+    dfree(k.coeff);
+    dfree(k.newton);
+    dfree(k.cdef);
+    dfree(k.cdef2);
+    k.nrhs = k.kmax = k.jcap = k.nblk = 0;
+    k.prec = -1;
+}
+
+static void free_deflation(ovs_gauge_s* g) {
+    dfree(g->R64);
+    dfree(g->L64);
+    dfree(g->R32);
+    dfree(g->L32);
+    dfree(g->sgn);
+    g->m = 0;
+    g->lambda.clear();
+}
+
+static int ensure_vec(ovs_gauge_s* g, int nrhs, int tprec) {
+    VecWork& w = g->vw;
+    if (w.nrhs >= nrhs && w.prec == tprec) return OVS_OK;
+    const int n = std::max(nrhs, w.prec == tprec ? w.nrhs : 0);
+    free_vec(w);
+    const size_t fb = field_bytes(g->N, tprec), f64 = field_bytes(g->N, PREC_F64);
+    CK(dalloc(&w.xint, fb * n));
+    CK(dalloc(&w.wvec, fb * n));
+    CK(dalloc(&w.yacc, f64 * n));
+    CK(dalloc(&w.sx, f64 * n));
+    CK(dalloc(&w.sy, f64 * n));
+    w.nrhs = n;
+    w.prec = tprec;
+    return OVS_OK;
+}
+
+static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
+    KryWork& k = g->kw;
+    const int jneed = std::max(kmax + 1, g->m);
+    const BlasPlan plan = blas_plan(field_units(g->N, tprec), nrhs, g->num_sms);
+    const BlasPlan plan1 = blas_plan(field_units(g->N, tprec), 1, g->num_sms);
+    const int nblk_need = std::max(plan.nblk, plan1.nblk);
+    if (k.prec == tprec && k.nrhs >= nrhs && k.kmax >= kmax && k.jcap >= jneed && k.nblk >= nblk_need) return OVS_OK;
+    const bool same = (k.prec == tprec);
+    const int n = std::max(nrhs, same ? k.nrhs : 0);
+    const int km = std::max(kmax, same ? k.kmax : 0);
+    const int jc = std::max(std::max(km + 1, g->m), jneed);
+    const int nb = std::max(nblk_need, blas_plan(field_units(g->N, tprec), 1, g->num_sms).nblk);
+    free_kry(k);
+    const size_t fb = field_bytes(g->N, tprec);
+    CK(dalloc(&k.basis, fb * (size_t)(km + 1) * n));
+    CK(dalloc(&k.H, sizeof(double2) * (size_t)(km + 1) * km * n));
+    CK(dalloc(&k.htmp, sizeof(double2) * (size_t)jc * n));
+    CK(dalloc(&k.partial, sizeof(double2) * (size_t)nb * jc * n));
+    CK(dalloc(&k.norm_part, sizeof(double) * (size_t)nb * n));
+    CK(dalloc(&k.beta, sizeof(double) * n));
+    CK(dalloc(&k.inv_beta, sizeof(double) * n));
+    CK(dalloc(&k.hnorm2, sizeof(double) * n));
+    CK(dalloc(&k.active, sizeof(int) * n));
+    CK(dalloc(&k.k_used, sizeof(int) * n));
+    CK(dalloc(&k.iters, sizeof(int) * n));
+    CK(dalloc(&k.status, sizeof(int) * n));
+    CK(dalloc(&k.coeff, sizeof(double2) * (size_t)km * n));
+    CK(dalloc(&k.newton, sizeof(double2) * 2 * (size_t)km * km * n));
+    CK(dalloc(&k.cdef, sizeof(double2) * (size_t)std::max(g->m, 1) * n));
+    CK(dalloc(&k.cdef2, sizeof(double2) * (size_t)std::max(g->m, 1) * n));
+    k.nrhs = n;
+    k.kmax = km;
+    k.jcap = jc;
+    k.nblk = nb;
+    k.prec = tprec;
+    return OVS_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int check_dims(const int32_t dims[4]) {
+    if (!dims) return fail(OVS_EINVAL, "dims is NULL");
+    long long v = 1;
+    for (int i = 0; i < 4; ++i) {
+        if (dims[i] < 2) return fail(OVS_EINVAL, "lattice extent %d of direction %d is below 2", dims[i], i);
+        v *= dims[i];
+    }
+    if (v * 12 > (1LL << 31) - 1) return fail(OVS_EINVAL, "lattice too large (12 V must fit in 31 bits)");
+    return OVS_OK;
+}
+
+static int new_handle(const int32_t dims[4], const double* links_host, int32_t prec, ovs_gauge_t* out) {
+    if (!out) return fail(OVS_EINVAL, "out is NULL");
+    *out = nullptr;
+    TRY(check_dims(dims));
+    if (prec != OVS_F64 && prec != OVS_MIXED) return fail(OVS_EINVAL, "prec must be OVS_F64 or OVS_MIXED");
+    ovs_gauge_s* g = new ovs_gauge_s();
+    for (int i = 0; i < 4; ++i) g->dims[i] = dims[i];
+    g->geom = make_geom(dims);
+    g->V = g->geom.V;
+    g->N = 12 * g->V;
+    g->prec = prec;
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    void* tmp = nullptr;
+    const size_t lb = (size_t)g->V * 72 * sizeof(double);
+    cudaError_t e = cudaMalloc(&g->links64, (size_t)g->V * 36 * sizeof(double2));
+    if (e == cudaSuccess && prec == OVS_MIXED) e = cudaMalloc(&g->links32, (size_t)g->V * 36 * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, lb);
+    if (e == cudaSuccess) e = cudaMemcpy(tmp, links_host, lb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_links_to_internal(tmp, g->links64, g->links32, (int)g->V, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        ovs_destroy(g);
+        return fail(e == cudaErrorMemoryAllocation ? OVS_ENOMEM : OVS_ECUDA, "gauge upload: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = g;
+    return OVS_OK;
+}
+
+// ----------------------------------------------------------------- ABI
+extern "C" {
+
+const char* ovs_last_error(void) { return g_err.c_str(); }
+
+const char* ovs_version(void) { return "ovsign 0.1 (sm_103a)"; }
+
+int ovs_create_gauge(const int32_t dims[4], uint64_t seed, double eps, int32_t prec, ovs_gauge_t* out) {
+    TRY(check_dims(dims));
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(OVS_EINVAL, "eps must be finite and >= 0");
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    std::vector<double> links((size_t)V * 72);
+    generate_links(V, seed, eps, links.data());
+    return new_handle(dims, links.data(), prec, out);
+}
+
+int ovs_create_gauge_from_links(const int32_t dims[4], const double* links, int32_t prec, ovs_gauge_t* out) {
+    if (!links) return fail(OVS_EINVAL, "links is NULL");
+    return new_handle(dims, links, prec, out);
+}
+
+int ovs_get_links(ovs_gauge_t g, double* links_out) {
+    if (!g || !links_out) return fail(OVS_EINVAL, "NULL argument");
+    void* tmp = nullptr;
+    const size_t lb = (size_t)g->V * 72 * sizeof(double);
+    CK(cudaMalloc(&tmp, lb));
+    cudaError_t e = launch_links_to_canonical(g->links64, tmp, (int)g->V, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(links_out, tmp, lb, cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    CK(e);
+    return OVS_OK;
+}
+
+int ovs_set_mu(ovs_gauge_t g, double mu, double m_w) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (!std::isfinite(mu) || !std::isfinite(m_w) || 8.0 + 2.0 * m_w == 0.0)
+        return fail(OVS_EINVAL, "mu and m_w must be finite and 8 + 2 m_w != 0");
+    g->mu = mu;
+    g->m_w = m_w;
+    g->kappa = 1.0 / (8.0 + 2.0 * m_w);
+    g->mu_set = true;
+    free_deflation(g);
+    return OVS_OK;
+}
+
+int ovs_matvec(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, int32_t prec, void* stream) {
+    if (!g || !x || !y) return fail(OVS_EINVAL, "NULL argument");
+    if (nrhs < 0) return fail(OVS_EINVAL, "nrhs < 0");
+    if (nrhs == 0) return OVS_OK;
+    if (op != OVS_OP_DW && op != OVS_OP_HW && op != OVS_OP_HW2) return fail(OVS_EINVAL, "bad op");
+    if (prec != OVS_F64 && prec != OVS_MIXED) return fail(OVS_EINVAL, "bad prec");
+    if (prec == OVS_MIXED && g->prec != OVS_MIXED) return fail(OVS_ESTATE, "handle was created without OVS_MIXED");
+    if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tp = tprec_of(prec);
+    TRY(ensure_vec(g, nrhs, tp));
+    const long long N = g->N;
+    const size_t f64 = field_bytes(N, PREC_F64), fb = field_bytes(N, tp);
+    const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+    const void* xd = x;
+    if (!xdev) {
+        CK(cudaMemcpyAsync(g->vw.sx, x, f64 * nrhs, cudaMemcpyHostToDevice, st));
+        xd = g->vw.sx;
+    }
+    void* yd = ydev ? y : g->vw.sy;
+    VecWork& w = g->vw;
+    CK(launch_to_internal(tp, xd, N, w.xint, fb, (int)g->V, nrhs, st));
+    const void* L = links_for(g, tp);
+    if (op == OVS_OP_HW2) {
+        CK(launch_wilson(tp, true, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
+        CK(launch_wilson(tp, true, L, w.wvec, fb, w.xint, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
+        CK(launch_to_canonical(tp, w.xint, fb, yd, N, (int)g->V, nrhs, st));
+    } else {
+        CK(launch_wilson(tp, op == OVS_OP_HW, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr,
+                         st));
+        CK(launch_to_canonical(tp, w.wvec, fb, yd, N, (int)g->V, nrhs, st));
+    }
+    if (!ydev) {
+        CK(cudaMemcpyAsync(y, yd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return OVS_OK;
+}
+
+// ------------------------------------------------------------ deflation
+static void host_inverse(std::vector<std::complex<double>>& a, int n, bool& ok) {
+    // Gauss-Jordan with partial pivoting, row-major, in place
+    std::vector<int> perm(n);
+    ok = true;
+    for (int p = 0; p < n; ++p) {
+        int piv = p;
+        double best = std::abs(a[(size_t)p * n + p]);
+        for (int i = p + 1; i < n; ++i)
+            if (std::abs(a[(size_t)i * n + p]) > best) { best = std::abs(a[(size_t)i * n + p]); piv = i; }
+        if (!(best > 0.0)) { ok = false; return; }
+        perm[p] = piv;
+        if (piv != p)
+            for (int j = 0; j < n; ++j) std::swap(a[(size_t)p * n + j], a[(size_t)piv * n + j]);
+        const std::complex<double> inv = 1.0 / a[(size_t)p * n + p];
+        for (int j = 0; j < n; ++j) a[(size_t)p * n + j] *= inv;
+        a[(size_t)p * n + p] = inv;
+        for (int i = 0; i < n; ++i) {
+            if (i == p) continue;
+            const std::complex<double> f = a[(size_t)i * n + p];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j)
+                if (j != p) a[(size_t)i * n + j] -= f * a[(size_t)p * n + j];
+            a[(size_t)i * n + p] = -f * inv;
+        }
+    }
+    for (int p = n - 1; p >= 0; --p)
+        if (perm[p] != p)
+            for (int i = 0; i < n; ++i) std::swap(a[(size_t)i * n + p], a[(size_t)i * n + perm[p]]);
+}
+
+namespace ovs {
+// Install R (right vectors) and L (left vectors), both device canonical
+// complex128 [m][N]; biorthonormalise L; keep FP32 copies for OVS_MIXED.
+int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, const double* lambda) {
+    free_deflation(g);
+    if (m == 0) return OVS_OK;
+    double lmax = 0.0;
+    for (int i = 0; i < m; ++i) lmax = std::max(lmax, std::hypot(lambda[2 * i], lambda[2 * i + 1]));
+    std::vector<double> sg(m);
+    for (int i = 0; i < m; ++i) {
+        if (!(std::fabs(lambda[2 * i]) > 1e-12 * lmax))
+            return fail(OVS_ESIGN, "deflated eigenvalue %d has Re lambda = %g: sign undefined", i, lambda[2 * i]);
+        sg[i] = lambda[2 * i] > 0 ? 1.0 : -1.0;
+    }
+    const long long N = g->N;
+    const int V = (int)g->V;
+    const size_t f64 = field_bytes(N, PREC_F64);
+    CK(dalloc(&g->R64, f64 * m));
+    CK(dalloc(&g->L64, f64 * m));
+    CK(dalloc(&g->sgn, sizeof(double) * m));
+    CK(cudaMemcpy(g->sgn, sg.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+    void* Ltmp = nullptr;
+    CK(dalloc(&Ltmp, f64 * m));
+    CK(launch_to_internal(PREC_F64, Rc, N, g->R64, f64, V, m, 0));
+    CK(launch_to_internal(PREC_F64, Lc, N, Ltmp, f64, V, m, 0));
+    // G[j][i] = L_j^+ R_i  (right-hand side i = R_i, basis = L shared)
+    const BlasPlan plan = blas_plan(N, m, g->num_sms);
+    void* part = nullptr;
+    void* G = nullptr;
+    CK(dalloc(&part, sizeof(double2) * (size_t)plan.nblk * m * m));
+    CK(dalloc(&G, sizeof(double2) * (size_t)m * m));
+    CK(launch_dots(PREC_F64, Ltmp, 0, N, m, g->R64, N, N, plan, m, part, nullptr, 0));
+    CK(launch_reduce(part, plan.nblk, m, m, G, m, false, nullptr, 0));
+    std::vector<std::complex<double>> gh((size_t)m * m), a((size_t)m * m);
+    CK(cudaMemcpy(gh.data(), G, sizeof(double2) * (size_t)m * m, cudaMemcpyDeviceToHost));
+    // gh[i*m + j] = L_j^+ R_i = G_ji with G = L^+ R. Row-major a = G.
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) a[(size_t)j * m + i] = gh[(size_t)i * m + j];
+    bool ok = true;
+    host_inverse(a, m, ok);
+    if (!ok) {
+        cudaFree(part); cudaFree(G); cudaFree(Ltmp);
+        return fail(OVS_EINVAL, "L^+ R is singular: left and right vectors do not span dual spaces");
+    }
+    // Lbi = L G^{-+}: Lbi_i = sum_j L_j (G^{-+})_{j i} = sum_j L_j conj(Ginv_{i j})
+    std::vector<std::complex<double>> cf((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) cf[(size_t)i * m + j] = std::conj(a[(size_t)i * m + j]);
+    CK(cudaMemcpy(G, cf.data(), sizeof(double2) * (size_t)m * m, cudaMemcpyHostToDevice));
+    CK(launch_update(PREC_F64, PREC_F64, Ltmp, 0, N, m, nullptr, G, m, 1.0, nullptr, 0, g->L64, N, N, plan, m,
+                     nullptr, nullptr, 0));
+    CK(cudaDeviceSynchronize());
+    cudaFree(part);
+    cudaFree(G);
+    if (g->prec == OVS_MIXED) {
+        const size_t f32 = field_bytes(N, PREC_F32);
+        CK(dalloc(&g->R32, f32 * m));
+        CK(dalloc(&g->L32, f32 * m));
+        CK(launch_to_internal(PREC_F32, Rc, N, g->R32, f32, V, m, 0));
+        CK(launch_to_canonical(PREC_F64, g->L64, f64, Ltmp, N, V, m, 0));
+        CK(launch_to_internal(PREC_F32, Ltmp, N, g->L32, f32, V, m, 0));
+        CK(cudaDeviceSynchronize());
+    }
+    cudaFree(Ltmp);
+    g->m = m;
+    g->lambda.assign(lambda, lambda + 2 * m);
+    return OVS_OK;
+}
+}  // namespace ovs
+
+int ovs_deflate_load(ovs_gauge_t g, int32_t m, const double* R, const double* L, const double* lambda) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
+    if (m < 0 || (long long)m > g->N) return fail(OVS_EINVAL, "m out of range");
+    if (m > 0 && (!R || !L || !lambda)) return fail(OVS_EINVAL, "NULL R, L or lambda");
+    if (m == 0) {
+        free_deflation(g);
+        return OVS_OK;
+    }
+    const size_t f64 = field_bytes(g->N, PREC_F64);
+    void *Rd = nullptr, *Ld = nullptr;
+    CK(dalloc(&Rd, f64 * m));
+    cudaError_t e = dalloc(&Ld, f64 * m);
+    if (e == cudaSuccess) e = cudaMemcpy(Rd, R, f64 * m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(Ld, L, f64 * m, cudaMemcpyHostToDevice);
+    int rc = OVS_OK;
+    if (e != cudaSuccess) rc = fail(OVS_ECUDA, "deflate_load upload: %s", cudaGetErrorString(e));
+    if (rc == OVS_OK) rc = install_deflation(g, m, Rd, Ld, lambda);
+    cudaFree(Rd);
+    cudaFree(Ld);
+    return rc;
+}
+
+int ovs_deflate_get(ovs_gauge_t g, int32_t* m_out, double* R, double* L, double* lambda) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (m_out) *m_out = g->m;
+    const int m = g->m;
+    if (m == 0) return OVS_OK;
+    if (lambda) std::memcpy(lambda, g->lambda.data(), sizeof(double) * 2 * m);
+    const size_t f64 = field_bytes(g->N, PREC_F64);
+    void* tmp = nullptr;
+    if (R || L) CK(dalloc(&tmp, f64 * m));
+    if (R) {
+        CK(launch_to_canonical(PREC_F64, g->R64, f64, tmp, g->N, (int)g->V, m, 0));
+        CK(cudaMemcpy(R, tmp, f64 * m, cudaMemcpyDeviceToHost));
+    }
+    if (L) {
+        CK(launch_to_canonical(PREC_F64, g->L64, f64, tmp, g->N, (int)g->V, m, 0));
+        CK(cudaMemcpy(L, tmp, f64 * m, cudaMemcpyDeviceToHost));
+    }
+    if (tmp) cudaFree(tmp);
+    return OVS_OK;
+}
+
+static uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+struct DeflHeader {
+    char magic[8];
+    int32_t dims[4];
+    double mu, m_w;
+    int64_t m, N;
+    uint64_t checksum;
+};
+
+int ovs_deflate_save(ovs_gauge_t g, const char* path) {
+    if (!g || !path) return fail(OVS_EINVAL, "NULL argument");
+    if (g->m == 0) return fail(OVS_ESTATE, "no deflation basis installed");
+    const int m = g->m;
+    const size_t f64 = field_bytes(g->N, PREC_F64);
+    std::vector<double> R((size_t)m * g->N * 2), L((size_t)m * g->N * 2), lam(2 * m);
+    TRY(ovs_deflate_get(g, nullptr, R.data(), L.data(), lam.data()));
+    DeflHeader h;
+    std::memcpy(h.magic, "OVSDEFL1", 8);
+    for (int i = 0; i < 4; ++i) h.dims[i] = g->dims[i];
+    h.mu = g->mu;
+    h.m_w = g->m_w;
+    h.m = m;
+    h.N = g->N;
+    uint64_t c = 1469598103934665603ULL;
+    c = fnv1a(lam.data(), lam.size() * sizeof(double), c);
+    c = fnv1a(R.data(), f64 * m, c);
+    c = fnv1a(L.data(), f64 * m, c);
+    h.checksum = c;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(OVS_EIO, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    ok = ok && std::fwrite(lam.data(), sizeof(double), lam.size(), f) == lam.size();
+    ok = ok && std::fwrite(R.data(), 1, f64 * m, f) == f64 * m;
+    ok = ok && std::fwrite(L.data(), 1, f64 * m, f) == f64 * m;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(OVS_EIO, "write to %s failed", path);
+    return OVS_OK;
+}
+
+int ovs_deflate_restore(ovs_gauge_t g, const char* path) {
+    if (!g || !path) return fail(OVS_EINVAL, "NULL argument");
+    if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(OVS_EIO, "cannot open %s", path);
+    DeflHeader h;
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "OVSDEFL1", 8) != 0) {
+        std::fclose(f);
+        return fail(OVS_EIO, "%s is not a deflation file", path);
+    }
+    bool same = h.N == g->N && h.mu == g->mu && h.m_w == g->m_w && h.m > 0 && h.m <= g->N;
+    for (int i = 0; i < 4; ++i) same = same && h.dims[i] == g->dims[i];
+    if (!same) {
+        std::fclose(f);
+        return fail(OVS_ESTATE, "%s was saved for another lattice, mu or m_w", path);
+    }
+    const int m = (int)h.m;
+    const size_t f64 = field_bytes(g->N, PREC_F64);
+    std::vector<double> R((size_t)m * g->N * 2), L((size_t)m * g->N * 2), lam(2 * m);
+    bool ok = std::fread(lam.data(), sizeof(double), lam.size(), f) == lam.size();
+    ok = ok && std::fread(R.data(), 1, f64 * m, f) == f64 * m;
+    ok = ok && std::fread(L.data(), 1, f64 * m, f) == f64 * m;
+    std::fclose(f);
+    if (!ok) return fail(OVS_EIO, "%s is truncated", path);
+    uint64_t c = 1469598103934665603ULL;
+    c = fnv1a(lam.data(), lam.size() * sizeof(double), c);
+    c = fnv1a(R.data(), f64 * m, c);
+    c = fnv1a(L.data(), f64 * m, c);
+    if (c != h.checksum) return fail(OVS_EIO, "%s: checksum mismatch", path);
+    return ovs_deflate_load(g, m, R.data(), L.data(), lam.data());
+}
+
+int ovs_deflate_setup(ovs_gauge_t g, int32_t m, double tol, double* eig_out) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
+    if (m <= 0 || (long long)m * 4 > g->N) return fail(OVS_EINVAL, "m must be in [1, N/4]");
+    if (!(tol > 0.0)) return fail(OVS_EINVAL, "tol must be > 0");
+    return eig_setup(g, m, tol, eig_out);
+}
+
+// ---------------------------------------------------------- sign apply
+int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
+                   ovs_apply_info* info, void* stream) {
+    if (!g || !x || !y || !opts) return fail(OVS_EINVAL, "NULL argument");
+    if (nrhs <= 0) return fail(OVS_EINVAL, "nrhs must be >= 1");
+    if (nrhs > 65535) return fail(OVS_EINVAL, "nrhs must be <= 65535");
+    if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
+    const int k = opts->k_max;
+    if (k < 1 || k > 2000) return fail(OVS_EINVAL, "k_max must be in [1, 2000]");
+    if ((long long)k + 1 > g->N) return fail(OVS_EINVAL, "k_max must be < N");
+    if (opts->prec != OVS_F64 && opts->prec != OVS_MIXED) return fail(OVS_EINVAL, "bad prec");
+    if (opts->prec == OVS_MIXED && g->prec != OVS_MIXED) return fail(OVS_ESTATE, "handle was created without OVS_MIXED");
+    if (opts->check_every != 0) return fail(OVS_EINVAL, "check_every > 0 needs the batched form");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tp = tprec_of(opts->prec);
+    TRY(ensure_vec(g, nrhs, tp));
+    TRY(ensure_kry(g, nrhs, k, tp));
+    VecWork& w = g->vw;
+    KryWork& kw = g->kw;
+    const long long N = g->N;
+    const int V = (int)g->V;
+    const size_t fb = field_bytes(N, tp), f64 = field_bytes(N, PREC_F64);
+    const long long units = field_units(N, tp);
+    const long long kmax = kw.kmax;
+    const long long basis_rhs_units = (kmax + 1) * units;
+    const size_t basis_rhs_bytes = (size_t)(kmax + 1) * fb;
+    const int ldh = (int)(kmax + 1);
+    const long long h_rhs = (long long)(kmax + 1) * kmax;
+    const BlasPlan plan = blas_plan(units, nrhs, g->num_sms);
+    const BlasPlan plan64 = blas_plan(N, nrhs, g->num_sms);
+    char* basis = (char*)kw.basis;
+
+    // input, canonical complex128 -> internal precision
+    const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+    const void* xd = x;
+    if (!xdev) {
+        CK(cudaMemcpyAsync(w.sx, x, f64 * nrhs, cudaMemcpyHostToDevice, st));
+        xd = w.sx;
+    }
+    void* yd = ydev ? y : w.sy;
+    CK(launch_to_internal(tp, xd, N, w.xint, fb, V, nrhs, st));
+    CK(cudaMemsetAsync(kw.H, 0, sizeof(double2) * h_rhs * nrhs, st));
+
+    // K5: LR projection (Sec. 5.3 step iii) and the exact deflated part
+    const int m = g->m;
+    if (m > 0) {
+        const void* Lb = tp == PREC_F64 ? g->L64 : g->L32;
+        const void* Rb = tp == PREC_F64 ? g->R64 : g->R32;
+        CK(launch_dots(tp, Lb, 0, units, m, w.xint, units, units, plan, nrhs, kw.partial, nullptr, st));
+        CK(launch_reduce(kw.partial, plan.nblk, m, nrhs, kw.cdef, m, false, nullptr, st));
+        CK(launch_sign_scale(kw.cdef, g->sgn, m, nrhs, kw.cdef2, st));
+        CK(launch_update(tp, tp, Rb, 0, units, m, nullptr, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, plan, nrhs,
+                         nullptr, nullptr, st));
+        // y = R sgn(Lambda) c in complex128 from the FP64 copy of R
+        CK(launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cdef2, m, 1.0, nullptr, 0, w.yacc, N, N,
+                         plan64, nrhs, nullptr, nullptr, st));
+    } else {
+        CK(cudaMemsetAsync(w.yacc, 0, f64 * nrhs, st));
+    }
+    // beta = ||x_ominus||, v_1 = x_ominus / beta (Sec. 5.3, Eq. LRArnoldi)
+    CK(launch_update(tp, tp, basis, 0, units, 0, nullptr, kw.coeff, 0, 0.0, w.xint, N, w.xint, N, units, plan, nrhs,
+                     kw.norm_part, nullptr, st));
+    CK(launch_init_beta(kw.norm_part, plan.nblk, nrhs, kw.beta, kw.inv_beta, kw.hnorm2, kw.active, kw.k_used, st));
+    CK(launch_scale(tp, w.xint, units, basis, basis_rhs_units, units, kw.inv_beta, nrhs, kw.active, st));
+
+    // Arnoldi with CGS2 (Sec. 4, Eq. Arnoldi)
+    for (int j = 0; j < k; ++j) {
+        const int J = j + 1;
+        char* vj = basis + (size_t)j * fb;
+        CK(launch_wilson(tp, true, links_for(g, tp), vj, basis_rhs_bytes, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
+                         kw.active, st));
+        double2* Hcol = (double2*)kw.H + (size_t)j * ldh;
+        CK(launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
+                       st));
+        CK(launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, false, kw.active, st));
+        CK(launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, Hcol, h_rhs, -1.0, w.wvec, N,
+                         w.wvec, N, units, plan, nrhs, nullptr, kw.active, st));
+        CK(launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
+                       st));
+        CK(launch_reduce(kw.partial, plan.nblk, J, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
+        CK(launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, true, kw.active, st));
+        CK(launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, kw.htmp, kw.jcap, -1.0, w.wvec, N,
+                         w.wvec, N, units, plan, nrhs, kw.norm_part, kw.active, st));
+        CK(launch_finalize(kw.norm_part, plan.nblk, nrhs, kw.H, h_rhs, ldh, j, kw.hnorm2, kw.inv_beta, kw.active,
+                           kw.k_used, st));
+        if (j + 1 < k)
+            CK(launch_scale(tp, w.wvec, units, basis + (size_t)(j + 1) * fb, basis_rhs_units, units, kw.inv_beta,
+                            nrhs, kw.active, st));
+    }
+    // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v)
+    CK(launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.coeff, kmax, kw.newton, (int)kmax, nrhs, kw.iters,
+                     kw.status, st));
+    // K4: y += V_k c (Sec. 5.3 step vi)
+    CK(launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
+                     w.yacc, N, units, plan, nrhs, nullptr, nullptr, st));
+    CK(launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
+    if (!ydev) CK(cudaMemcpyAsync(y, yd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
+    g->last_nrhs = nrhs;
+    g->last_stream = st;
+    if (info) return ovs_get_info(g, info, nrhs);
+    if (!ydev) CK(cudaStreamSynchronize(st));
+    return OVS_OK;
+}
+
+int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
+    if (!g || !info) return fail(OVS_EINVAL, "NULL argument");
+    if (nrhs <= 0 || nrhs > g->last_nrhs) return fail(OVS_EINVAL, "nrhs exceeds the last application");
+    CK(cudaStreamSynchronize(g->last_stream));
+    std::vector<int> ku(nrhs), it(nrhs), stt(nrhs);
+    std::vector<double> beta(nrhs);
+    CK(cudaMemcpy(ku.data(), g->kw.k_used, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(it.data(), g->kw.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(stt.data(), g->kw.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(beta.data(), g->kw.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+    int worst = OVS_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        info[r].k_used = ku[r];
+        info[r].newton_iters = it[r];
+        info[r].status = stt[r];
+        info[r].reserved = 0;
+        info[r].beta = beta[r];
+        info[r].est_err = 0.0;
+        if (stt[r] == OVS_ESIGN) worst = OVS_ESIGN;
+        else if (stt[r] == OVS_NOT_CONVERGED && worst == OVS_OK) worst = OVS_NOT_CONVERGED;
+    }
+    return worst;
+}
+
+void ovs_destroy(ovs_gauge_t g) {
+    if (!g) return;
+    free_deflation(g);
+    free_vec(g->vw);
+    free_kry(g->kw);
+    dfree(g->links64);
+    dfree(g->links32);
+    delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,312 @@
+// K1: the Wilson-Dirac stencil at chemical potential, H_w(mu) = gamma5 D_w(mu)
+// (Sec. 2, Eqs. Dov and Dw), and K7: field layout conversions.
+//
+// One thread per (site, right-hand side). Each of the eight hops projects
+// the neighbour's 4-spinor onto the rank-2 subspace of (1 -/+ gamma_nu)
+// (a 2 x 3 half spinor), multiplies the two colour vectors by U (forward)
+// or U^+ (backward), scales by kappa-independent factors (e^{+/-mu} on
+// temporal hops, -1 on hops that wrap in t) and adds the reconstructed
+// 4-spinor. The diagonal term and gamma5 are applied in the store.
+//
+// Chiral basis: gamma_k = [[0, -i s_k], [i s_k, 0]], gamma_4 = [[0,1],[1,0]],
+// so with upper = spins (0,1) and lower = spins (2,3):
+//   (1 - gamma_k) psi = [h; -i s_k h],   h = psi_up + i s_k psi_dn
+//   (1 + gamma_k) psi = [h;  i s_k h],   h = psi_up - i s_k psi_dn
+//   (1 - gamma_4) psi = [h; -h],         h = psi_up - psi_dn
+//   (1 + gamma_4) psi = [h;  h],         h = psi_up + psi_dn
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ovs {
+
+// ------------------------------------------------------------- field access
+template <typename R> struct Field;
+template <> struct Field<double> {
+    __device__ __forceinline__ static void load(const void* f, int V, int s, cd (&p)[12]) {
+        const double2* d = static_cast<const double2*>(f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const double2* u = d + 2 * ((size_t)q * V + s);
+            double2 a = __ldg(u), b = __ldg(u + 1);
+            p[2 * q] = {a.x, a.y};
+            p[2 * q + 1] = {b.x, b.y};
+        }
+    }
+    __device__ __forceinline__ static void store(void* f, int V, int s, const cd (&p)[12]) {
+        double2* d = static_cast<double2*>(f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            double2* u = d + 2 * ((size_t)q * V + s);
+            u[0] = make_double2(p[2 * q].re, p[2 * q].im);
+            u[1] = make_double2(p[2 * q + 1].re, p[2 * q + 1].im);
+        }
+    }
+    __device__ __forceinline__ static void link(const void* u, int V, int nu, int s, cd (&m)[9]) {
+        const double2* d = static_cast<const double2*>(u) + (size_t)nu * 9 * V;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            double2 v = __ldg(d + (size_t)e * V + s);
+            m[e] = {v.x, v.y};
+        }
+    }
+};
+template <> struct Field<float> {
+    __device__ __forceinline__ static void load(const void* f, int V, int s, cf (&p)[12]) {
+        const float4* d = static_cast<const float4*>(f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            float4 v = __ldg(d + (size_t)q * V + s);
+            p[2 * q] = {v.x, v.y};
+            p[2 * q + 1] = {v.z, v.w};
+        }
+    }
+    __device__ __forceinline__ static void store(void* f, int V, int s, const cf (&p)[12]) {
+        float4* d = static_cast<float4*>(f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            d[(size_t)q * V + s] = make_float4(p[2 * q].re, p[2 * q].im, p[2 * q + 1].re, p[2 * q + 1].im);
+    }
+    __device__ __forceinline__ static void link(const void* u, int V, int nu, int s, cf (&m)[9]) {
+        const float2* d = static_cast<const float2*>(u) + (size_t)nu * 9 * V;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            float2 v = __ldg(d + (size_t)e * V + s);
+            m[e] = {v.x, v.y};
+        }
+    }
+};
+
+// --------------------------------------------------------------------- hops
+// Forward hop: acc += (1 - gamma_NU) * fac * U * psi
+template <int NU, typename R>
+__device__ __forceinline__ void hop_fwd(const cplx<R> (&p)[12], const cplx<R> (&U)[9], R fac, cplx<R> (&acc)[12]) {
+    cplx<R> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<R> a0 = p[c], a1 = p[3 + c], a2 = p[6 + c], a3 = p[9 + c];
+        if (NU == 0) { h0[c] = a0 + ti(a3); h1[c] = a1 + ti(a2); }
+        if (NU == 1) { h0[c] = a0 + a3;     h1[c] = a1 - a2; }
+        if (NU == 2) { h0[c] = a0 + ti(a2); h1[c] = a1 - ti(a3); }
+        if (NU == 3) { h0[c] = a0 - a2;     h1[c] = a1 - a3; }
+        h0[c] = h0[c] * fac;
+        h1[c] = h1[c] * fac;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cplx<R> u0 = {R(0), R(0)}, u1 = {R(0), R(0)};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            cfma(u0, U[3 * a + b], h0[b]);
+            cfma(u1, U[3 * a + b], h1[b]);
+        }
+        acc[a] = acc[a] + u0;
+        acc[3 + a] = acc[3 + a] + u1;
+        if (NU == 0) { acc[6 + a] = acc[6 + a] + tmi(u1); acc[9 + a] = acc[9 + a] + tmi(u0); }
+        if (NU == 1) { acc[6 + a] = acc[6 + a] - u1;      acc[9 + a] = acc[9 + a] + u0; }
+        if (NU == 2) { acc[6 + a] = acc[6 + a] + tmi(u0); acc[9 + a] = acc[9 + a] + ti(u1); }
+        if (NU == 3) { acc[6 + a] = acc[6 + a] - u0;      acc[9 + a] = acc[9 + a] - u1; }
+    }
+}
+
+// Backward hop: acc += (1 + gamma_NU) * fac * U^+ * psi, U the link of the
+// backward neighbour in direction NU.
+template <int NU, typename R>
+__device__ __forceinline__ void hop_bwd(const cplx<R> (&p)[12], const cplx<R> (&U)[9], R fac, cplx<R> (&acc)[12]) {
+    cplx<R> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<R> a0 = p[c], a1 = p[3 + c], a2 = p[6 + c], a3 = p[9 + c];
+        if (NU == 0) { h0[c] = a0 + tmi(a3); h1[c] = a1 + tmi(a2); }
+        if (NU == 1) { h0[c] = a0 - a3;      h1[c] = a1 + a2; }
+        if (NU == 2) { h0[c] = a0 + tmi(a2); h1[c] = a1 + ti(a3); }
+        if (NU == 3) { h0[c] = a0 + a2;      h1[c] = a1 + a3; }
+        h0[c] = h0[c] * fac;
+        h1[c] = h1[c] * fac;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cplx<R> u0 = {R(0), R(0)}, u1 = {R(0), R(0)};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            cfmac(u0, U[3 * b + a], h0[b]);
+            cfmac(u1, U[3 * b + a], h1[b]);
+        }
+        acc[a] = acc[a] + u0;
+        acc[3 + a] = acc[3 + a] + u1;
+        if (NU == 0) { acc[6 + a] = acc[6 + a] + ti(u1); acc[9 + a] = acc[9 + a] + ti(u0); }
+        if (NU == 1) { acc[6 + a] = acc[6 + a] + u1;     acc[9 + a] = acc[9 + a] - u0; }
+        if (NU == 2) { acc[6 + a] = acc[6 + a] + ti(u0); acc[9 + a] = acc[9 + a] + tmi(u1); }
+        if (NU == 3) { acc[6 + a] = acc[6 + a] + u0;     acc[9 + a] = acc[9 + a] + u1; }
+    }
+}
+
+template <int NU, typename R>
+__device__ __forceinline__ void both_hops(const void* links, const void* in, const Geom& g, int s, int coord,
+                                          R efwd, R ebwd, cplx<R> (&acc)[12]) {
+    const int L = g.L[NU], st = g.stride[NU];
+    const int sf = (coord == L - 1) ? s - (L - 1) * st : s + st;
+    const int sb = (coord == 0) ? s + (L - 1) * st : s - st;
+    R ff = efwd, fb = ebwd;
+    if (NU == 3) {
+        if (coord == L - 1) ff = -ff;  // antiperiodic in time
+        if (coord == 0) fb = -fb;
+    }
+    cplx<R> U[9], p[12];
+    Field<R>::link(links, g.V, NU, s, U);
+    Field<R>::load(in, g.V, sf, p);
+    hop_fwd<NU>(p, U, ff, acc);
+    Field<R>::link(links, g.V, NU, sb, U);
+    Field<R>::load(in, g.V, sb, p);
+    hop_bwd<NU>(p, U, fb, acc);
+}
+
+// out_r = [gamma5] (in_r - kappa * hops(in_r)) for r = blockIdx.y.
+// in/out strides are in bytes between right-hand sides.
+template <typename R, bool G5>
+__global__ void __launch_bounds__(128) k_wilson(const void* __restrict__ links, const char* __restrict__ in,
+                                                char* __restrict__ out, size_t in_stride, size_t out_stride, Geom g,
+                                                R kappa, R emu, R emmu, const int* __restrict__ active) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (s >= g.V) return;
+    if (active != nullptr && active[r] == 0) return;
+    const void* inr = in + r * in_stride;
+    void* outr = out + r * out_stride;
+    int c = s;
+    const int x = c % g.L[0]; c /= g.L[0];
+    const int y = c % g.L[1]; c /= g.L[1];
+    const int z = c % g.L[2];
+    const int t = c / g.L[2];
+    cplx<R> acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = {R(0), R(0)};
+    both_hops<0, R>(links, inr, g, s, x, R(1), R(1), acc);
+    both_hops<1, R>(links, inr, g, s, y, R(1), R(1), acc);
+    both_hops<2, R>(links, inr, g, s, z, R(1), R(1), acc);
+    both_hops<3, R>(links, inr, g, s, t, emu, emmu, acc);
+    cplx<R> p[12];
+    Field<R>::load(inr, g.V, s, p);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        cplx<R> v = p[q] - acc[q] * kappa;
+        if (G5 && q >= 6) v = -v;
+        p[q] = v;
+    }
+    Field<R>::store(outr, g.V, s, p);
+}
+
+// ------------------------------------------------------------ layouts (K7)
+// canonical complex128 [nrhs][V][12]  ->  internal planes of precision R
+template <typename R>
+__global__ void k_to_internal(const double2* __restrict__ canon, size_t canon_stride, char* __restrict__ out,
+                              size_t out_stride, int V) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (s >= V) return;
+    const double2* src = canon + r * canon_stride + (size_t)s * 12;
+    cplx<R> p[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        double2 v = src[q];
+        p[q] = {R(v.x), R(v.y)};
+    }
+    Field<R>::store(out + r * out_stride, V, s, p);
+}
+
+// internal planes of precision R -> canonical complex128
+template <typename R>
+__global__ void k_to_canonical(const char* __restrict__ in, size_t in_stride, double2* __restrict__ canon,
+                               size_t canon_stride, int V) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (s >= V) return;
+    cplx<R> p[12];
+    Field<R>::load(in + r * in_stride, V, s, p);
+    double2* dst = canon + r * canon_stride + (size_t)s * 12;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) dst[q] = make_double2(double(p[q].re), double(p[q].im));
+}
+
+// canonical links complex128 [V][4][3][3] -> planes [nu][e][V] (complex128 and,
+// if u32 != nullptr, complex64)
+__global__ void k_links_to_internal(const double2* __restrict__ canon, double2* __restrict__ u64,
+                                    float2* __restrict__ u32, int V) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            double2 v = canon[((size_t)s * 4 + nu) * 9 + e];
+            u64[((size_t)nu * 9 + e) * V + s] = v;
+            if (u32 != nullptr) u32[((size_t)nu * 9 + e) * V + s] = make_float2(float(v.x), float(v.y));
+        }
+}
+
+__global__ void k_links_to_canonical(const double2* __restrict__ u64, double2* __restrict__ canon, int V) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) canon[((size_t)s * 4 + nu) * 9 + e] = u64[((size_t)nu * 9 + e) * V + s];
+}
+
+// ------------------------------------------------------------- host launch
+static inline dim3 site_grid(int V, int nrhs, int threads) { return dim3((V + threads - 1) / threads, nrhs); }
+
+cudaError_t launch_wilson(int prec, bool gamma5, const void* links, const void* in, size_t in_stride, void* out,
+                          size_t out_stride, const Geom& g, int nrhs, double kappa, double mu, const int* active,
+                          cudaStream_t st) {
+    const int T = 128;
+    dim3 grid = site_grid(g.V, nrhs, T);
+    const double emu = exp(mu), emmu = exp(-mu);
+    if (prec == PREC_F64) {
+        if (gamma5)
+            k_wilson<double, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
+                                                       kappa, emu, emmu, active);
+        else
+            k_wilson<double, false><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
+                                                        kappa, emu, emmu, active);
+    } else {
+        if (gamma5)
+            k_wilson<float, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
+                                                      (float)kappa, (float)emu, (float)emmu, active);
+        else
+            k_wilson<float, false><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
+                                                       (float)kappa, (float)emu, (float)emmu, active);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_internal(int prec, const void* canon, size_t canon_stride_cplx, void* out, size_t out_stride,
+                               int V, int nrhs, cudaStream_t st) {
+    dim3 grid = site_grid(V, nrhs, 128);
+    if (prec == PREC_F64)
+        k_to_internal<double><<<grid, 128, 0, st>>>((const double2*)canon, canon_stride_cplx, (char*)out, out_stride, V);
+    else
+        k_to_internal<float><<<grid, 128, 0, st>>>((const double2*)canon, canon_stride_cplx, (char*)out, out_stride, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_canonical(int prec, const void* in, size_t in_stride, void* canon, size_t canon_stride_cplx,
+                                int V, int nrhs, cudaStream_t st) {
+    dim3 grid = site_grid(V, nrhs, 128);
+    if (prec == PREC_F64)
+        k_to_canonical<double><<<grid, 128, 0, st>>>((const char*)in, in_stride, (double2*)canon, canon_stride_cplx, V);
+    else
+        k_to_canonical<float><<<grid, 128, 0, st>>>((const char*)in, in_stride, (double2*)canon, canon_stride_cplx, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_to_internal(const void* canon, void* u64, void* u32, int V, cudaStream_t st) {
+    k_links_to_internal<<<(V + 127) / 128, 128, 0, st>>>((const double2*)canon, (double2*)u64, (float2*)u32, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_to_canonical(const void* u64, void* canon, int V, cudaStream_t st) {
+    k_links_to_canonical<<<(V + 127) / 128, 128, 0, st>>>((const double2*)u64, (double2*)canon, V);
+    return cudaGetLastError();
+}
+
+}  // namespace ovs
