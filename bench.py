@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Throughput of y = sgn(H_w(mu)) x: mixed-precision batched form vs plain FP64.
+
+Workload (default): 16^3 x 32 lattice (N = 1,572,864), synthetic SU(3)
+field U = exp(i eps X) with eps = 0.6 and seed 5, mu = 0.1, m_w = -1.5,
+LR deflation of m = 100 critical eigenvectors (set-up timed separately),
+Krylov dimension k = 250, 16 complex Gaussian right-hand sides of unit norm.
+One step = one ovs_sign_apply of the 16 right-hand sides in the mixed form
+(complex64 links, matvec and Krylov basis; FP64 Gram-Schmidt accumulation,
+Hessenberg matrix, deflation coefficients and Newton sign). The same
+application in plain FP64 with one right-hand side is timed beside it and
+the mixed result of that right-hand side is checked against it (relative
+2-norm <= 1e-6).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sgn(H_w(μ))x applications/s at 1e-6 rel err, mixed+batched vs plain FP64"
+UNIT = "applications/s"
+DEFAULT = dict(dims=(16, 16, 16, 32), eps=0.6, seed=5, mu=0.1, m_w=-1.5, m=100, k=250, nrhs=16, src_seed=2,
+               eig_tol=1e-8)
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--dims", type=int, nargs=4, default=None)
+    p.add_argument("--m", type=int, default=None)
+    p.add_argument("--k", type=int, default=None)
+    p.add_argument("--nrhs", type=int, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    w = dict(DEFAULT)
+    if args.dims:
+        w["dims"] = tuple(args.dims)
+    for key in ("m", "k", "nrhs"):
+        if getattr(args, key) is not None:
+            w[key] = getattr(args, key)
+    w["V"] = w["dims"][0] * w["dims"][1] * w["dims"][2] * w["dims"][3]
+    w["N"] = 12 * w["V"]
+    d = w["dims"]
+    w["name"] = (f"{d[0]}^3x{d[3]}" if d[0] == d[1] == d[2] else "x".join(map(str, d))) + \
+        f" LR-deflated sgn(H_w(mu))x, m={w['m']}, k={w['k']}, {w['nrhs']} RHS, mixed+batched"
+    return w
+
+
+def config_of(w, world):
+    return {
+        "workload": w["name"],
+        "lattice": list(w["dims"]), "N": w["N"], "gauge": f"U=exp(i eps X), eps={w['eps']}, seed={w['seed']}",
+        "mu": w["mu"], "m_w": w["m_w"], "m_deflated": w["m"], "k": w["k"], "nrhs_per_gpu": w["nrhs"],
+        "global_batch": w["nrhs"] * world,
+        "precision": "complex64 links/matvec/Krylov basis; FP64 Gram-Schmidt accumulation, Hessenberg, "
+                     "deflation coefficients, Newton sign",
+        "l2": "inputs larger than L2: the Krylov basis streamed every step is "
+              f"{w['nrhs'] * (w['k'] + 1) * w['N'] * 8 / 1e9:.1f} GB per GPU",
+        "parallelism": f"replicas x{world} (independent right-hand-side batches)",
+    }
+
+
+# --------------------------------------------------------------- distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, local, backend):
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------- CPU baseline
+def cpu_sample(w, k_sample, seed_offset=0):
+    """Time the oracle on a bounded sample of one application and scale it.
+
+    Sample: one right-hand side of the full lattice; the oracle's LR
+    deflation with m random (biorthonormalised) vectors and its CGS2
+    Arnoldi run for k_sample steps. The matvec and Gram-Schmidt costs are
+    measured separately and scaled to k steps as t = t0 + k t_mv +
+    c k(k+1)/2 (CGS2 sweeps grow linearly with the step), the Newton cost
+    as (k / k_sample)^3. Returns (seconds per application, description).
+    """
+    import numpy as np
+
+    import synth
+    from oracle import deflation, lattice, newton
+
+    links = synth.gauge_links(w["dims"], w["seed"], w["eps"])
+    h = lattice.hw_operator(links, w["dims"], w["mu"], w["m_w"])
+    n = w["N"]
+    rng = np.random.default_rng(1234 + seed_offset)
+    m = w["m"]
+    r = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
+    l_ = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
+    lam = rng.standard_normal(m) + 0.5j * rng.standard_normal(m) if m else None
+    x = synth.gaussian_vectors(n, 1, w["src_seed"] + seed_offset)[0]
+    t_mv = [0.0]
+
+    def mv(v):
+        t = time.perf_counter()
+        out = h @ v
+        t_mv[0] += time.perf_counter() - t
+        return out
+
+    t0 = time.perf_counter()
+    _, info = deflation.lr_sign_apply(mv, x, r, l_, lam, k_sample)
+    total = time.perf_counter() - t0
+    tn = time.perf_counter()
+    newton.roberts_sign(info["H"][:k_sample, :k_sample])
+    t_newton = time.perf_counter() - tn
+    ks, k = k_sample, w["k"]
+    per_mv = t_mv[0] / ks
+    t_cgs = max(total - t_mv[0] - t_newton, 0.0)
+    # deflation projection: two sweeps of m vectors plus biorthonormalisation,
+    # measured apart from the Arnoldi loop by a second call with k = 1
+    t1 = time.perf_counter()
+    deflation.lr_sign_apply(lambda v: h @ v, x, r, l_, lam, 1)
+    t_setup = time.perf_counter() - t1 - per_mv
+    t_cgs_loop = max(t_cgs - t_setup, 0.0)
+    c = t_cgs_loop / (ks * (ks + 1) / 2)
+    t_app = t_setup + k * per_mv + c * k * (k + 1) / 2 + t_newton * (k / ks) ** 3
+    desc = (f"1 RHS of the full lattice: LR projection (m={m}) + {ks} of {k} CGS2 Arnoldi steps "
+            f"timed ({total:.1f} s), scaled to k={k} as t0 + k*t_mv + c*k(k+1)/2 "
+            f"(t_mv={per_mv:.3f} s, c={c:.2e} s); numpy/scipy FP64")
+    return t_app, desc
+
+
+def cpu_cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args, w, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_0704_3486_gb300 as ovs
+    import synth
+
+    if not os.path.exists(ovs.LIB_PATH):
+        from paper_0704_3486_gb300 import build
+        build.build()
+    ovs.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist_init(world, local, "nccl")
+    stream = torch.cuda.current_stream()
+
+    g = ovs.create_gauge(w["dims"], w["seed"], w["eps"], ovs.MIXED)
+    ovs.set_mu(g, w["mu"], w["m_w"])
+    setup = {"m": w["m"], "seconds": 0.0, "status": "none"}
+    if w["m"] > 0:
+        t0 = time.perf_counter()
+        lam, st = ovs.deflate_setup(g, w["m"], w["eig_tol"])
+        torch.cuda.synchronize()
+        setup = {"m": w["m"], "seconds": time.perf_counter() - t0, "status": ovs.STATUS.get(st, st),
+                 "min_abs_re_lambda": float(np.min(np.abs(lam.real))),
+                 "max_abs_lambda": float(np.max(np.abs(lam)))}
+    x_host = synth.gaussian_vectors(w["N"], w["nrhs"], w["src_seed"] + 1000 * rank)
+    x = torch.from_numpy(x_host).to(dev)
+    y = torch.empty_like(x)
+    k = w["k"]
+
+    for _ in range(args.warmup):
+        ovs.sign_apply(g, x, y, k, prec=ovs.MIXED, stream=stream, want_info=False)
+    torch.cuda.synchronize()
+    ovs.profile_enable(g, timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ovs.sign_apply(g, x, y, k, prec=ovs.MIXED, stream=stream, want_info=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    prof = ovs.profile_read(g)
+    ovs.profile_enable(g, timing=False)
+    status, info = ovs.get_info(g, w["nrhs"])
+    ms_max = max_over_ranks(ms_total, world, dev)
+    value = w["nrhs"] * args.steps * world / (ms_max / 1e3)
+
+    # plain FP64, one right-hand side, same (m, k): time it and check the
+    # mixed result of that right-hand side against it
+    x0 = x[:1].contiguous()
+    y64 = torch.empty_like(x0)
+    ovs.sign_apply(g, x0, y64, k, prec=ovs.F64, stream=stream, want_info=False)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    n64 = 2
+    f0.record(stream)
+    for _ in range(n64):
+        ovs.sign_apply(g, x0, y64, k, prec=ovs.F64, stream=stream, want_info=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_value = n64 / (f0.elapsed_time(f1) / 1e3)
+    rel_err = float(torch.linalg.norm(y[0] - y64[0]) / torch.linalg.norm(y64[0]))
+
+    # end to end through the C ABI with pinned host buffers: H2D of x and
+    # D2H of y inside the timed region (the library stages host pointers)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ovs.sign_apply(g, xh, yh, k, prec=ovs.MIXED, stream=stream, want_info=False)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+        nbytes = x_host.size * 16
+        e2e = {"value": w["nrhs"] * args.steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    # roofline of the dominant kernel class (device time share in the timed region)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured"
+    if peak is None:
+        peak, peak_src = 6800.0, "fallback"
+    top = max(("dots", "update", "matvec"), key=lambda c: prof[c]["ms"])
+    ach = prof[top]["bytes"] / (prof[top]["ms"] / 1e3) / 1e9 if prof[top]["ms"] > 0 else 0.0
+    share = {c: round(prof[c]["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-9), 4) for c in prof}
+    roofline = {"bound": "hbm", "kernel": {"dots": "k_dots (CGS2 inner products)",
+                                            "update": "k_update (CGS2 update / recombination)",
+                                            "matvec": "k_wilson (H_w stencil)"}[top],
+                "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "peak_source": f"{peak_src} hbm_gbs (copy)", "traffic": None,
+                "per_class": {c: {"ms_per_step": round(prof[c]["ms"] / args.steps, 3),
+                                  "launches_per_step": prof[c]["launches"] // max(args.steps, 1),
+                                  "gbs": round(prof[c]["bytes"] / (prof[c]["ms"] / 1e3) / 1e9, 1)
+                                  if prof[c]["ms"] > 0 else None,
+                                  "share": share[c]} for c in prof}}
+    launches = sum(p["launches"] for p in prof.values())
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(w, world),
+        "fp64_single_rhs": {"value": round(fp64_value, 4), "unit": UNIT, "rel_err_mixed_vs_fp64": rel_err,
+                            "within_1e-6": rel_err <= 1e-6,
+                            "speedup_mixed_batched": round(value / world / fp64_value, 3)},
+        "deflation_setup": setup,
+        "apply_info": {"k_used": sorted({i["k_used"] for i in info}),
+                       "newton_iters": sorted({i["newton_iters"] for i in info}),
+                       "status": ovs.STATUS.get(status, status)},
+        "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
+    }
+    g.destroy()
+    return out
+
+
+def run_reference(args, w, world, rank):
+    """CPU oracle on bounded samples; rank 0 only (other ranks exit)."""
+    if rank != 0:
+        return None
+    k_sample = 8
+    times = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        t_app, desc = cpu_sample(w, k_sample, seed_offset=i)
+        if i >= args.warmup:
+            times.append(t_app)
+    t = statistics.median(times)
+    value = 1.0 / t
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    w = workload(args)
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, w, world, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_ours(args, w, world, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            t_app, desc = cpu_sample(w, 8)
+            out["cpu_baseline"] = {"value": 1.0 / t_app, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -177,6 +177,31 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
 /* Reports of the last ovs_sign_apply on this handle (waits for its stream). */
 int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs);
 
+/* Tracing. Every kernel a handle launches is counted per class, together
+ * with its algorithmic bytes (the bytes the operation must move at least:
+ * each operand read once, each result written once). With timing on, every
+ * launch is also bracketed by two CUDA events on its stream, so per-class
+ * device times can be read back; this costs two event records per launch
+ * and no host synchronisation except when the event pool (8192 launches)
+ * fills up. */
+enum {
+    OVS_PROF_MATVEC = 0, /* K1: H_w / D_w stencil */
+    OVS_PROF_DOTS = 1,   /* K2: Gram-Schmidt inner products (also L^+ x) */
+    OVS_PROF_UPDATE = 2, /* K2/K4/K5: basis updates, recombination, projection */
+    OVS_PROF_SMALL = 3,  /* reductions, Hessenberg column, norms, scaling */
+    OVS_PROF_NEWTON = 4, /* K3: Roberts iteration on H_k */
+    OVS_PROF_LAYOUT = 5, /* K7: canonical <-> internal layout */
+    OVS_PROF_NCLASS = 6
+};
+
+/* Reset the counters; timing != 0 turns event timing on, 0 turns it off. */
+int ovs_profile_enable(ovs_gauge_t g, int32_t timing);
+
+/* Totals since the last ovs_profile_enable (any pointer may be NULL):
+ * ms[c] device milliseconds (0 without timing), launches[c], bytes[c]
+ * algorithmic bytes, for c < OVS_PROF_NCLASS. Waits for timed launches. */
+int ovs_profile_read(ovs_gauge_t g, double* ms, int64_t* launches, double* bytes);
+
 /* Thread-local message of the last error (never NULL). */
 const char* ovs_last_error(void);
 

@@ -27,8 +27,10 @@ STATUS = {
 EXPORTS = [
     "ovs_create_gauge", "ovs_create_gauge_from_links", "ovs_get_links", "ovs_set_mu", "ovs_matvec",
     "ovs_deflate_setup", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
-    "ovs_sign_apply", "ovs_get_info", "ovs_last_error", "ovs_version", "ovs_destroy",
+    "ovs_sign_apply", "ovs_get_info", "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
+    "ovs_destroy",
 ]
+PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout"]
 
 
 class OvsError(RuntimeError):
@@ -79,6 +81,8 @@ def load(path=None):
         "ovs_deflate_restore": ([vp, ctypes.c_char_p], i32),
         "ovs_sign_apply": ([vp, vp, vp, i32, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp], i32),
         "ovs_get_info": ([vp, ctypes.POINTER(ApplyInfo), i32], i32),
+        "ovs_profile_enable": ([vp, i32], i32),
+        "ovs_profile_read": ([vp, vp, vp, vp], i32),
         "ovs_last_error": ([], ctypes.c_char_p),
         "ovs_version": ([], ctypes.c_char_p),
         "ovs_destroy": ([vp], None),
@@ -243,6 +247,22 @@ def get_info(g, nrhs):
     info = (ApplyInfo * nrhs)()
     st = _check(load().ovs_get_info(g.handle, info, int(nrhs)))
     return st, [i.as_dict() for i in info]
+
+
+def profile_enable(g, timing=True):
+    _check(load().ovs_profile_enable(g.handle, 1 if timing else 0))
+
+
+def profile_read(g):
+    """Per kernel class: {'matvec': {'ms':..., 'launches':..., 'bytes':...}, ...}."""
+    import numpy as np
+    n = len(PROF_CLASSES)
+    ms = np.zeros(n, dtype=np.float64)
+    launches = np.zeros(n, dtype=np.int64)
+    nbytes = np.zeros(n, dtype=np.float64)
+    _check(load().ovs_profile_read(g.handle, _ptr(ms), _ptr(launches), _ptr(nbytes)))
+    return {c: {"ms": float(ms[i]), "launches": int(launches[i]), "bytes": float(nbytes[i])}
+            for i, c in enumerate(PROF_CLASSES)}
 
 
 def version():

@@ -120,12 +120,77 @@ struct ovs_gauge_s {
     KryWork kw;
     int last_nrhs = 0;
     cudaStream_t last_stream = nullptr;
+    // tracing (ovs_profile_*)
+    struct Pending {
+        int cls, ev;
+    };
+    bool timing = false;
+    double prof_ms[OVS_PROF_NCLASS] = {};
+    double prof_bytes[OVS_PROF_NCLASS] = {};
+    long long prof_launches[OVS_PROF_NCLASS] = {};
+    std::vector<cudaEvent_t> events;
+    std::vector<Pending> pending;
+    cudaStream_t prof_stream = nullptr;
 };
 
 // helpers exposed to other translation units of the library
 namespace ovs {
 int lib_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 }  // namespace ovs
+
+// ------------------------------------------------------------- tracing
+static const int kEventPool = 16384;
+
+static void prof_flush(ovs_gauge_s* g) {
+    if (g->pending.empty()) return;
+    cudaEventSynchronize(g->events[g->pending.back().ev + 1]);
+    for (const auto& p : g->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, g->events[p.ev], g->events[p.ev + 1]) == cudaSuccess) g->prof_ms[p.cls] += t;
+    }
+    cudaGetLastError();
+    g->pending.clear();
+}
+
+static void prof_begin(ovs_gauge_s* g, int cls, cudaStream_t st) {
+    ++g->prof_launches[cls];
+    if (!g->timing) return;
+    if (g->events.empty()) {
+        g->events.resize(kEventPool);
+        for (auto& e : g->events) cudaEventCreate(&e);
+    }
+    if ((int)(2 * g->pending.size() + 2) > kEventPool) prof_flush(g);
+    const int ev = (int)(2 * g->pending.size());
+    g->pending.push_back({cls, ev});
+    cudaEventRecord(g->events[ev], st);
+}
+
+static void prof_end(ovs_gauge_s* g, int cls, double bytes, cudaStream_t st) {
+    g->prof_bytes[cls] += bytes;
+    if (!g->timing) return;
+    cudaEventRecord(g->events[g->pending.back().ev + 1], st);
+}
+
+// Launch `call` as a kernel of tracing class `cls` moving `bytes` algorithmic bytes.
+#define KL(cls, bytes, call)              \
+    do {                                  \
+        prof_begin(g, (cls), st);         \
+        CK(call);                         \
+        prof_end(g, (cls), (bytes), st);  \
+    } while (0)
+
+static double sz_of(int tprec) { return tprec == PREC_F64 ? 16.0 : 8.0; }
+// K1: links read once, each right-hand side read and written once
+static double bytes_wilson(long long V, int tp, int nrhs) { return (double)V * sz_of(tp) * (36.0 + 24.0 * nrhs); }
+// K2 dot sweep: J basis vectors (shared or per rhs) and w
+static double bytes_dots(long long N, int tp, int J, int nrhs, bool shared) {
+    return (double)N * sz_of(tp) * ((shared ? J : (double)J * nrhs) + nrhs);
+}
+// update sweep: J basis vectors, optional input, output
+static double bytes_update(long long N, int tpv, int tpo, int J, int nrhs, bool shared, bool has_in) {
+    return (double)N * (sz_of(tpv) * (shared ? J : (double)J * nrhs) + sz_of(tpo) * nrhs * (has_in ? 2.0 : 1.0));
+}
+static double bytes_layout(long long N, int tp, int nrhs) { return (double)N * nrhs * (16.0 + sz_of(tp)); }
 
 static size_t field_bytes(long long N, int tprec) { return (size_t)N * (tprec == PREC_F64 ? 16 : 8); }
 static long long field_units(long long N, int tprec) { return tprec == PREC_F64 ? N : N / 2; }
@@ -344,16 +409,20 @@ int ovs_matvec(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, 
     }
     void* yd = ydev ? y : g->vw.sy;
     VecWork& w = g->vw;
-    CK(launch_to_internal(tp, xd, N, w.xint, fb, (int)g->V, nrhs, st));
+    const double bl = bytes_layout(N, tp, nrhs), bw = bytes_wilson(g->V, tp, nrhs);
+    KL(OVS_PROF_LAYOUT, bl, launch_to_internal(tp, xd, N, w.xint, fb, (int)g->V, nrhs, st));
     const void* L = links_for(g, tp);
     if (op == OVS_OP_HW2) {
-        CK(launch_wilson(tp, true, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
-        CK(launch_wilson(tp, true, L, w.wvec, fb, w.xint, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
-        CK(launch_to_canonical(tp, w.xint, fb, yd, N, (int)g->V, nrhs, st));
+        KL(OVS_PROF_MATVEC, bw,
+           launch_wilson(tp, true, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
+        KL(OVS_PROF_MATVEC, bw,
+           launch_wilson(tp, true, L, w.wvec, fb, w.xint, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
+        KL(OVS_PROF_LAYOUT, bl, launch_to_canonical(tp, w.xint, fb, yd, N, (int)g->V, nrhs, st));
     } else {
-        CK(launch_wilson(tp, op == OVS_OP_HW, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr,
+        KL(OVS_PROF_MATVEC, bw,
+           launch_wilson(tp, op == OVS_OP_HW, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr,
                          st));
-        CK(launch_to_canonical(tp, w.wvec, fb, yd, N, (int)g->V, nrhs, st));
+        KL(OVS_PROF_LAYOUT, bl, launch_to_canonical(tp, w.wvec, fb, yd, N, (int)g->V, nrhs, st));
     }
     if (!ydev) {
         CK(cudaMemcpyAsync(y, yd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
@@ -397,6 +466,7 @@ namespace ovs {
 // Install R (right vectors) and L (left vectors), both device canonical
 // complex128 [m][N]; biorthonormalise L; keep FP32 copies for OVS_MIXED.
 int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, const double* lambda) {
+    cudaStream_t st = 0;
     free_deflation(g);
     if (m == 0) return OVS_OK;
     double lmax = 0.0;
@@ -416,16 +486,16 @@ int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, con
     CK(cudaMemcpy(g->sgn, sg.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
     void* Ltmp = nullptr;
     CK(dalloc(&Ltmp, f64 * m));
-    CK(launch_to_internal(PREC_F64, Rc, N, g->R64, f64, V, m, 0));
-    CK(launch_to_internal(PREC_F64, Lc, N, Ltmp, f64, V, m, 0));
+    KL(OVS_PROF_LAYOUT, 0.0, launch_to_internal(PREC_F64, Rc, N, g->R64, f64, V, m, 0));
+    KL(OVS_PROF_LAYOUT, 0.0, launch_to_internal(PREC_F64, Lc, N, Ltmp, f64, V, m, 0));
     // G[j][i] = L_j^+ R_i  (right-hand side i = R_i, basis = L shared)
     const BlasPlan plan = blas_plan(N, m, g->num_sms);
     void* part = nullptr;
     void* G = nullptr;
     CK(dalloc(&part, sizeof(double2) * (size_t)plan.nblk * m * m));
     CK(dalloc(&G, sizeof(double2) * (size_t)m * m));
-    CK(launch_dots(PREC_F64, Ltmp, 0, N, m, g->R64, N, N, plan, m, part, nullptr, 0));
-    CK(launch_reduce(part, plan.nblk, m, m, G, m, false, nullptr, 0));
+    KL(OVS_PROF_DOTS, 0.0, launch_dots(PREC_F64, Ltmp, 0, N, m, g->R64, N, N, plan, m, part, nullptr, 0));
+    KL(OVS_PROF_SMALL, 0.0, launch_reduce(part, plan.nblk, m, m, G, m, false, nullptr, 0));
     std::vector<std::complex<double>> gh((size_t)m * m), a((size_t)m * m);
     CK(cudaMemcpy(gh.data(), G, sizeof(double2) * (size_t)m * m, cudaMemcpyDeviceToHost));
     // gh[i*m + j] = L_j^+ R_i = G_ji with G = L^+ R. Row-major a = G.
@@ -442,7 +512,7 @@ int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, con
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < m; ++j) cf[(size_t)i * m + j] = std::conj(a[(size_t)i * m + j]);
     CK(cudaMemcpy(G, cf.data(), sizeof(double2) * (size_t)m * m, cudaMemcpyHostToDevice));
-    CK(launch_update(PREC_F64, PREC_F64, Ltmp, 0, N, m, nullptr, G, m, 1.0, nullptr, 0, g->L64, N, N, plan, m,
+    KL(OVS_PROF_UPDATE, 0.0, launch_update(PREC_F64, PREC_F64, Ltmp, 0, N, m, nullptr, G, m, 1.0, nullptr, 0, g->L64, N, N, plan, m,
                      nullptr, nullptr, 0));
     CK(cudaDeviceSynchronize());
     cudaFree(part);
@@ -451,9 +521,9 @@ int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, con
         const size_t f32 = field_bytes(N, PREC_F32);
         CK(dalloc(&g->R32, f32 * m));
         CK(dalloc(&g->L32, f32 * m));
-        CK(launch_to_internal(PREC_F32, Rc, N, g->R32, f32, V, m, 0));
-        CK(launch_to_canonical(PREC_F64, g->L64, f64, Ltmp, N, V, m, 0));
-        CK(launch_to_internal(PREC_F32, Ltmp, N, g->L32, f32, V, m, 0));
+        KL(OVS_PROF_LAYOUT, 0.0, launch_to_internal(PREC_F32, Rc, N, g->R32, f32, V, m, 0));
+        KL(OVS_PROF_LAYOUT, 0.0, launch_to_canonical(PREC_F64, g->L64, f64, Ltmp, N, V, m, 0));
+        KL(OVS_PROF_LAYOUT, 0.0, launch_to_internal(PREC_F32, Ltmp, N, g->L32, f32, V, m, 0));
         CK(cudaDeviceSynchronize());
     }
     cudaFree(Ltmp);
@@ -495,12 +565,13 @@ int ovs_deflate_get(ovs_gauge_t g, int32_t* m_out, double* R, double* L, double*
     const size_t f64 = field_bytes(g->N, PREC_F64);
     void* tmp = nullptr;
     if (R || L) CK(dalloc(&tmp, f64 * m));
+    cudaStream_t st = 0;
     if (R) {
-        CK(launch_to_canonical(PREC_F64, g->R64, f64, tmp, g->N, (int)g->V, m, 0));
+        KL(OVS_PROF_LAYOUT, 0.0, launch_to_canonical(PREC_F64, g->R64, f64, tmp, g->N, (int)g->V, m, 0));
         CK(cudaMemcpy(R, tmp, f64 * m, cudaMemcpyDeviceToHost));
     }
     if (L) {
-        CK(launch_to_canonical(PREC_F64, g->L64, f64, tmp, g->N, (int)g->V, m, 0));
+        KL(OVS_PROF_LAYOUT, 0.0, launch_to_canonical(PREC_F64, g->L64, f64, tmp, g->N, (int)g->V, m, 0));
         CK(cudaMemcpy(L, tmp, f64 * m, cudaMemcpyDeviceToHost));
     }
     if (tmp) cudaFree(tmp);
@@ -634,7 +705,7 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
         xd = w.sx;
     }
     void* yd = ydev ? y : w.sy;
-    CK(launch_to_internal(tp, xd, N, w.xint, fb, V, nrhs, st));
+    KL(OVS_PROF_LAYOUT, bytes_layout(N, tp, nrhs), launch_to_internal(tp, xd, N, w.xint, fb, V, nrhs, st));
     CK(cudaMemsetAsync(kw.H, 0, sizeof(double2) * h_rhs * nrhs, st));
 
     // K5: LR projection (Sec. 5.3 step iii) and the exact deflated part
@@ -642,54 +713,73 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
     if (m > 0) {
         const void* Lb = tp == PREC_F64 ? g->L64 : g->L32;
         const void* Rb = tp == PREC_F64 ? g->R64 : g->R32;
-        CK(launch_dots(tp, Lb, 0, units, m, w.xint, units, units, plan, nrhs, kw.partial, nullptr, st));
-        CK(launch_reduce(kw.partial, plan.nblk, m, nrhs, kw.cdef, m, false, nullptr, st));
-        CK(launch_sign_scale(kw.cdef, g->sgn, m, nrhs, kw.cdef2, st));
-        CK(launch_update(tp, tp, Rb, 0, units, m, nullptr, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, plan, nrhs,
+        KL(OVS_PROF_DOTS, bytes_dots(N, tp, m, nrhs, true),
+           launch_dots(tp, Lb, 0, units, m, w.xint, units, units, plan, nrhs, kw.partial, nullptr, st));
+        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * m * nrhs,
+           launch_reduce(kw.partial, plan.nblk, m, nrhs, kw.cdef, m, false, nullptr, st));
+        KL(OVS_PROF_SMALL, 32.0 * m * nrhs, launch_sign_scale(kw.cdef, g->sgn, m, nrhs, kw.cdef2, st));
+        KL(OVS_PROF_UPDATE, bytes_update(N, tp, tp, m, nrhs, true, true),
+           launch_update(tp, tp, Rb, 0, units, m, nullptr, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, plan, nrhs,
                          nullptr, nullptr, st));
         // y = R sgn(Lambda) c in complex128 from the FP64 copy of R
-        CK(launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cdef2, m, 1.0, nullptr, 0, w.yacc, N, N,
+        KL(OVS_PROF_UPDATE, bytes_update(N, PREC_F64, PREC_F64, m, nrhs, true, false),
+           launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cdef2, m, 1.0, nullptr, 0, w.yacc, N, N,
                          plan64, nrhs, nullptr, nullptr, st));
     } else {
         CK(cudaMemsetAsync(w.yacc, 0, f64 * nrhs, st));
     }
     // beta = ||x_ominus||, v_1 = x_ominus / beta (Sec. 5.3, Eq. LRArnoldi)
-    CK(launch_update(tp, tp, basis, 0, units, 0, nullptr, kw.coeff, 0, 0.0, w.xint, N, w.xint, N, units, plan, nrhs,
+    KL(OVS_PROF_UPDATE, bytes_update(N, tp, tp, 0, nrhs, false, true),
+       launch_update(tp, tp, basis, 0, units, 0, nullptr, kw.coeff, 0, 0.0, w.xint, N, w.xint, N, units, plan, nrhs,
                      kw.norm_part, nullptr, st));
-    CK(launch_init_beta(kw.norm_part, plan.nblk, nrhs, kw.beta, kw.inv_beta, kw.hnorm2, kw.active, kw.k_used, st));
-    CK(launch_scale(tp, w.xint, units, basis, basis_rhs_units, units, kw.inv_beta, nrhs, kw.active, st));
+    KL(OVS_PROF_SMALL, 8.0 * plan.nblk * nrhs,
+       launch_init_beta(kw.norm_part, plan.nblk, nrhs, kw.beta, kw.inv_beta, kw.hnorm2, kw.active, kw.k_used, st));
+    KL(OVS_PROF_SMALL, 2.0 * fb * nrhs,
+       launch_scale(tp, w.xint, units, basis, basis_rhs_units, units, kw.inv_beta, nrhs, kw.active, st));
 
     // Arnoldi with CGS2 (Sec. 4, Eq. Arnoldi)
+    const double bw = bytes_wilson(g->V, tp, nrhs);
     for (int j = 0; j < k; ++j) {
         const int J = j + 1;
         char* vj = basis + (size_t)j * fb;
-        CK(launch_wilson(tp, true, links_for(g, tp), vj, basis_rhs_bytes, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
+        KL(OVS_PROF_MATVEC, bw,
+           launch_wilson(tp, true, links_for(g, tp), vj, basis_rhs_bytes, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
                          kw.active, st));
         double2* Hcol = (double2*)kw.H + (size_t)j * ldh;
-        CK(launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
+        const double bd = bytes_dots(N, tp, J, nrhs, false), bu = bytes_update(N, tp, tp, J, nrhs, false, true);
+        const double br = 16.0 * plan.nblk * J * nrhs;
+        KL(OVS_PROF_DOTS, bd,
+           launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
                        st));
-        CK(launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, false, kw.active, st));
-        CK(launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, Hcol, h_rhs, -1.0, w.wvec, N,
-                         w.wvec, N, units, plan, nrhs, nullptr, kw.active, st));
-        CK(launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
+        KL(OVS_PROF_SMALL, br, launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, false, kw.active, st));
+        KL(OVS_PROF_UPDATE, bu,
+           launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, Hcol, h_rhs, -1.0, w.wvec, N, w.wvec, N,
+                         units, plan, nrhs, nullptr, kw.active, st));
+        KL(OVS_PROF_DOTS, bd,
+           launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
                        st));
-        CK(launch_reduce(kw.partial, plan.nblk, J, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
-        CK(launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, true, kw.active, st));
-        CK(launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, kw.htmp, kw.jcap, -1.0, w.wvec, N,
-                         w.wvec, N, units, plan, nrhs, kw.norm_part, kw.active, st));
-        CK(launch_finalize(kw.norm_part, plan.nblk, nrhs, kw.H, h_rhs, ldh, j, kw.hnorm2, kw.inv_beta, kw.active,
+        KL(OVS_PROF_SMALL, br, launch_reduce(kw.partial, plan.nblk, J, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
+        KL(OVS_PROF_SMALL, br, launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, true, kw.active, st));
+        KL(OVS_PROF_UPDATE, bu,
+           launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, kw.htmp, kw.jcap, -1.0, w.wvec, N, w.wvec,
+                         N, units, plan, nrhs, kw.norm_part, kw.active, st));
+        KL(OVS_PROF_SMALL, 8.0 * plan.nblk * nrhs + 16.0 * J * nrhs,
+           launch_finalize(kw.norm_part, plan.nblk, nrhs, kw.H, h_rhs, ldh, j, kw.hnorm2, kw.inv_beta, kw.active,
                            kw.k_used, st));
         if (j + 1 < k)
-            CK(launch_scale(tp, w.wvec, units, basis + (size_t)(j + 1) * fb, basis_rhs_units, units, kw.inv_beta,
+            KL(OVS_PROF_SMALL, 2.0 * fb * nrhs,
+               launch_scale(tp, w.wvec, units, basis + (size_t)(j + 1) * fb, basis_rhs_units, units, kw.inv_beta,
                             nrhs, kw.active, st));
     }
     // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v)
-    CK(launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.coeff, kmax, kw.newton, (int)kmax, nrhs, kw.iters,
+    KL(OVS_PROF_NEWTON, 16.0 * (double)k * k * nrhs,
+       launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.coeff, kmax, kw.newton, (int)kmax, nrhs, kw.iters,
                      kw.status, st));
     // K4: y += V_k c (Sec. 5.3 step vi)
-    CK(launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
+    KL(OVS_PROF_UPDATE, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
+       launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
                      w.yacc, N, units, plan, nrhs, nullptr, nullptr, st));
-    CK(launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
+    KL(OVS_PROF_LAYOUT, bytes_layout(N, PREC_F64, nrhs), launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
     if (!ydev) CK(cudaMemcpyAsync(y, yd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
     g->last_nrhs = nrhs;
     g->last_stream = st;
@@ -722,8 +812,33 @@ int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
     return worst;
 }
 
+int ovs_profile_enable(ovs_gauge_t g, int32_t timing) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    prof_flush(g);
+    for (int c = 0; c < OVS_PROF_NCLASS; ++c) {
+        g->prof_ms[c] = 0.0;
+        g->prof_bytes[c] = 0.0;
+        g->prof_launches[c] = 0;
+    }
+    g->timing = timing != 0;
+    return OVS_OK;
+}
+
+int ovs_profile_read(ovs_gauge_t g, double* ms, int64_t* launches, double* bytes) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    prof_flush(g);
+    for (int c = 0; c < OVS_PROF_NCLASS; ++c) {
+        if (ms) ms[c] = g->prof_ms[c];
+        if (launches) launches[c] = g->prof_launches[c];
+        if (bytes) bytes[c] = g->prof_bytes[c];
+    }
+    return OVS_OK;
+}
+
 void ovs_destroy(ovs_gauge_t g) {
     if (!g) return;
+    prof_flush(g);
+    for (auto& e : g->events) cudaEventDestroy(e);
     free_deflation(g);
     free_vec(g->vw);
     free_kry(g->kw);
