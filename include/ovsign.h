@@ -120,6 +120,18 @@ int ovs_matvec(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, 
  * installed and eig_out filled), ENOMEM, ECUDA. */
 int ovs_deflate_setup(ovs_gauge_t g, int32_t m, double tol, double* eig_out);
 
+/* Statistics of the last ovs_deflate_setup on this handle: iterations of
+ * the right (iters[0]) and left (iters[1]) subspace iterations, the total
+ * number of single-vector H_w applications, and the largest relative
+ * residual ||H r - lambda r|| / ||H|| of the installed right pairs (any
+ * pointer may be NULL). */
+int ovs_deflate_stats(ovs_gauge_t g, int32_t* iters, int64_t* matvecs, double* max_resid);
+
+/* Work limit of ovs_deflate_setup on this handle: wall-clock seconds for
+ * the whole set-up (0 = no limit; default 0). When the limit is reached the
+ * current Ritz pairs are installed and ovs_deflate_setup returns OVS_EEIG. */
+int ovs_set_setup_budget(ovs_gauge_t g, double max_seconds);
+
 /* Install a deflation basis given by the caller (host complex128 arrays
  * R and L of [m][N], lambda of 2m doubles). L is biorthonormalised against
  * R (L <- L (L^+ R)^-+). m = 0 removes deflation. Errors: EINVAL, ESTATE

@@ -26,7 +26,7 @@ STATUS = {
 }
 EXPORTS = [
     "ovs_create_gauge", "ovs_create_gauge_from_links", "ovs_get_links", "ovs_set_mu", "ovs_matvec",
-    "ovs_deflate_setup", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
+    "ovs_deflate_setup", "ovs_deflate_stats", "ovs_set_setup_budget", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
     "ovs_sign_apply", "ovs_get_info", "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
     "ovs_destroy",
 ]
@@ -75,6 +75,8 @@ def load(path=None):
         "ovs_set_mu": ([vp, dbl, dbl], i32),
         "ovs_matvec": ([vp, i32, vp, vp, i32, i32, vp], i32),
         "ovs_deflate_setup": ([vp, i32, dbl, vp], i32),
+        "ovs_deflate_stats": ([vp, vp, vp, vp], i32),
+        "ovs_set_setup_budget": ([vp, dbl], i32),
         "ovs_deflate_load": ([vp, i32, vp, vp, vp], i32),
         "ovs_deflate_get": ([vp, p_i32, vp, vp, vp], i32),
         "ovs_deflate_save": ([vp, ctypes.c_char_p], i32),
@@ -185,12 +187,29 @@ def matvec(g, op, x, y, nrhs=None, prec=F64, stream=None):
     _check(load().ovs_matvec(g.handle, int(op), _ptr(x), _ptr(y), int(nrhs), int(prec), _stream(stream)))
 
 
-def deflate_setup(g, m, tol=1e-10):
+def deflate_setup(g, m, tol=1e-10, allow_unconverged=False):
+    """Returns (eigenvalues, status). With allow_unconverged, OVS_EEIG (basis
+    installed but not at tol) is returned as a status instead of raised."""
     import numpy as np
     eig = np.empty(2 * m, dtype=np.float64)
     status = load().ovs_deflate_setup(g.handle, int(m), float(tol), _ptr(eig))
-    _check(status)
+    if not (allow_unconverged and status == -5):
+        _check(status)
     return eig[0::2] + 1j * eig[1::2], status
+
+
+def deflate_stats(g):
+    """{'iterations': (right, left), 'matvecs': n} of the last deflate_setup."""
+    import numpy as np
+    it = np.zeros(2, dtype=np.int32)
+    mv = np.zeros(1, dtype=np.int64)
+    rs = np.zeros(1, dtype=np.float64)
+    _check(load().ovs_deflate_stats(g.handle, _ptr(it), _ptr(mv), _ptr(rs)))
+    return {"iterations": (int(it[0]), int(it[1])), "matvecs": int(mv[0]), "max_resid": float(rs[0])}
+
+
+def set_setup_budget(g, max_seconds):
+    _check(load().ovs_set_setup_budget(g.handle, float(max_seconds)))
 
 
 def deflate_load(g, R, L, lam):

@@ -21,6 +21,7 @@
 #include "../../include/ovsign.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "handle.h"
 
 namespace ovs {
 void generate_links(long long V, uint64_t seed, double eps, double* links);
@@ -68,70 +69,6 @@ template <typename T> static void dfree(T*& p) {
     if (p) cudaFree((void*)p);
     p = nullptr;
 }
-
-struct VecWork {  // per-right-hand-side vectors
-    int nrhs = 0, prec = -1;
-    void* xint = nullptr;  // [nrhs][N] precision prec (x, then x_ominus)
-    void* wvec = nullptr;  // [nrhs][N] precision prec (Arnoldi w)
-    void* yacc = nullptr;  // [nrhs][N] complex128 internal (y accumulator)
-    void* sx = nullptr;    // [nrhs][N] complex128 canonical staging (host x)
-    void* sy = nullptr;    // [nrhs][N] complex128 canonical staging (host y)
-};
-
-struct KryWork {  // Krylov basis and small matrices
-    int nrhs = 0, kmax = 0, prec = -1, jcap = 0, nblk = 0;
-    void* basis = nullptr;       // [nrhs][kmax+1][N] precision prec
-    void* H = nullptr;           // [nrhs][(kmax+1) x kmax] complex128, column-major
-    void* htmp = nullptr;        // [nrhs][jcap] complex128
-    void* partial = nullptr;     // [nrhs][nblk][jcap] complex128
-    double* norm_part = nullptr; // [nrhs][nblk]
-    double* beta = nullptr;
-    double* inv_beta = nullptr;
-    double* hnorm2 = nullptr;
-    int* active = nullptr;
-    int* k_used = nullptr;
-    int* iters = nullptr;
-    int* status = nullptr;
-    void* coeff = nullptr;  // [nrhs][kmax] complex128
-    void* newton = nullptr; // [nrhs][2 kmax^2] complex128
-    void* cdef = nullptr;   // [nrhs][m] complex128 deflation coefficients
-    void* cdef2 = nullptr;  // [nrhs][m] complex128 sgn-scaled
-};
-
-struct ovs_gauge_s {
-    int dims[4];
-    Geom geom;
-    long long V = 0, N = 0;
-    int prec = OVS_F64;
-    int device = 0, num_sms = 148;
-    bool mu_set = false;
-    double mu = 0.0, m_w = 0.0, kappa = 0.0;
-    void* links64 = nullptr;  // [4][9][V] double2
-    void* links32 = nullptr;  // [4][9][V] float2 (OVS_MIXED)
-    // deflation basis (internal layout)
-    int m = 0;
-    void* R64 = nullptr;  // [m][N] double2 planes
-    void* L64 = nullptr;  // biorthonormalised
-    void* R32 = nullptr;  // [m][N/2] float4 planes
-    void* L32 = nullptr;
-    double* sgn = nullptr;  // device [m]
-    std::vector<double> lambda;  // host 2m
-    VecWork vw;
-    KryWork kw;
-    int last_nrhs = 0;
-    cudaStream_t last_stream = nullptr;
-    // tracing (ovs_profile_*)
-    struct Pending {
-        int cls, ev;
-    };
-    bool timing = false;
-    double prof_ms[OVS_PROF_NCLASS] = {};
-    double prof_bytes[OVS_PROF_NCLASS] = {};
-    long long prof_launches[OVS_PROF_NCLASS] = {};
-    std::vector<cudaEvent_t> events;
-    std::vector<Pending> pending;
-    cudaStream_t prof_stream = nullptr;
-};
 
 // helpers exposed to other translation units of the library
 namespace ovs {
@@ -192,6 +129,10 @@ static double bytes_update(long long N, int tpv, int tpo, int J, int nrhs, bool 
 }
 static double bytes_layout(long long N, int tp, int nrhs) { return (double)N * nrhs * (16.0 + sz_of(tp)); }
 
+// Largest Krylov dimension: the inner-product sweep keeps 8 warps x (2k+2)
+// complex128 accumulators in shared memory (<= 200 KB).
+static const int kMaxK = 790;
+
 static size_t field_bytes(long long N, int tprec) { return (size_t)N * (tprec == PREC_F64 ? 16 : 8); }
 static long long field_units(long long N, int tprec) { return tprec == PREC_F64 ? N : N / 2; }
 static int tprec_of(int prec) { return prec == OVS_MIXED ? PREC_F32 : PREC_F64; }
@@ -211,6 +152,7 @@ static void free_kry(KryWork& k) {
     dfree(k.basis);
     dfree(k.H);
     dfree(k.htmp);
+    dfree(k.dcoef);
     dfree(k.partial);
     dfree(k.norm_part);
     dfree(k.beta);
@@ -256,7 +198,7 @@ static int ensure_vec(ovs_gauge_s* g, int nrhs, int tprec) {
 
 static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     KryWork& k = g->kw;
-    const int jneed = std::max(kmax + 1, g->m);
+    const int jneed = std::max(gdots_stride(2, kmax), gdots_stride(1, std::max(kmax, g->m)));
     const BlasPlan plan = blas_plan(field_units(g->N, tprec), nrhs, g->num_sms);
     const BlasPlan plan1 = blas_plan(field_units(g->N, tprec), 1, g->num_sms);
     const int nblk_need = std::max(plan.nblk, plan1.nblk);
@@ -264,13 +206,14 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     const bool same = (k.prec == tprec);
     const int n = std::max(nrhs, same ? k.nrhs : 0);
     const int km = std::max(kmax, same ? k.kmax : 0);
-    const int jc = std::max(std::max(km + 1, g->m), jneed);
+    const int jc = std::max(gdots_stride(2, km), jneed);
     const int nb = std::max(nblk_need, blas_plan(field_units(g->N, tprec), 1, g->num_sms).nblk);
     free_kry(k);
     const size_t fb = field_bytes(g->N, tprec);
     CK(dalloc(&k.basis, fb * (size_t)(km + 1) * n));
     CK(dalloc(&k.H, sizeof(double2) * (size_t)(km + 1) * km * n));
     CK(dalloc(&k.htmp, sizeof(double2) * (size_t)jc * n));
+    CK(dalloc(&k.dcoef, sizeof(double2) * (size_t)n));
     CK(dalloc(&k.partial, sizeof(double2) * (size_t)nb * jc * n));
     CK(dalloc(&k.norm_part, sizeof(double) * (size_t)nb * n));
     CK(dalloc(&k.beta, sizeof(double) * n));
@@ -462,6 +405,8 @@ static void host_inverse(std::vector<std::complex<double>>& a, int n, bool& ok) 
             for (int i = 0; i < n; ++i) std::swap(a[(size_t)i * n + p], a[(size_t)i * n + perm[p]]);
 }
 
+}  // extern "C"
+
 namespace ovs {
 // Install R (right vectors) and L (left vectors), both device canonical
 // complex128 [m][N]; biorthonormalise L; keep FP32 copies for OVS_MIXED.
@@ -492,10 +437,12 @@ int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, con
     const BlasPlan plan = blas_plan(N, m, g->num_sms);
     void* part = nullptr;
     void* G = nullptr;
-    CK(dalloc(&part, sizeof(double2) * (size_t)plan.nblk * m * m));
+    const int S = gdots_stride(1, m);
+    CK(dalloc(&part, sizeof(double2) * (size_t)plan.nblk * S * m));
     CK(dalloc(&G, sizeof(double2) * (size_t)m * m));
-    KL(OVS_PROF_DOTS, 0.0, launch_dots(PREC_F64, Ltmp, 0, N, m, g->R64, N, N, plan, m, part, nullptr, 0));
-    KL(OVS_PROF_SMALL, 0.0, launch_reduce(part, plan.nblk, m, m, G, m, false, nullptr, 0));
+    KL(OVS_PROF_DOTS, 0.0,
+       launch_gdots(PREC_F64, 1, Ltmp, 0, N, m, g->R64, N, nullptr, 0, false, N, plan, m, part, nullptr, 0));
+    KL(OVS_PROF_SMALL, 0.0, launch_reduce(part, plan.nblk, S, m, m, G, m, false, nullptr, 0));
     std::vector<std::complex<double>> gh((size_t)m * m), a((size_t)m * m);
     CK(cudaMemcpy(gh.data(), G, sizeof(double2) * (size_t)m * m, cudaMemcpyDeviceToHost));
     // gh[i*m + j] = L_j^+ R_i = G_ji with G = L^+ R. Row-major a = G.
@@ -532,6 +479,8 @@ int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, con
     return OVS_OK;
 }
 }  // namespace ovs
+
+extern "C" {
 
 int ovs_deflate_load(ovs_gauge_t g, int32_t m, const double* R, const double* L, const double* lambda) {
     if (!g) return fail(OVS_EINVAL, "NULL handle");
@@ -657,6 +606,24 @@ int ovs_deflate_restore(ovs_gauge_t g, const char* path) {
     return ovs_deflate_load(g, m, R.data(), L.data(), lam.data());
 }
 
+int ovs_deflate_stats(ovs_gauge_t g, int32_t* iters, int64_t* matvecs, double* max_resid) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (iters) {
+        iters[0] = g->setup_iters[0];
+        iters[1] = g->setup_iters[1];
+    }
+    if (matvecs) *matvecs = g->setup_matvecs;
+    if (max_resid) *max_resid = g->setup_resid;
+    return OVS_OK;
+}
+
+int ovs_set_setup_budget(ovs_gauge_t g, double max_seconds) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (!(max_seconds >= 0.0)) return fail(OVS_EINVAL, "max_seconds must be >= 0");
+    g->setup_budget_s = max_seconds;
+    return OVS_OK;
+}
+
 int ovs_deflate_setup(ovs_gauge_t g, int32_t m, double tol, double* eig_out) {
     if (!g) return fail(OVS_EINVAL, "NULL handle");
     if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
@@ -673,7 +640,7 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
     if (nrhs > 65535) return fail(OVS_EINVAL, "nrhs must be <= 65535");
     if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
     const int k = opts->k_max;
-    if (k < 1 || k > 2000) return fail(OVS_EINVAL, "k_max must be in [1, 2000]");
+    if (k < 1 || k > kMaxK) return fail(OVS_EINVAL, "k_max must be in [1, %d]", kMaxK);
     if ((long long)k + 1 > g->N) return fail(OVS_EINVAL, "k_max must be < N");
     if (opts->prec != OVS_F64 && opts->prec != OVS_MIXED) return fail(OVS_EINVAL, "bad prec");
     if (opts->prec == OVS_MIXED && g->prec != OVS_MIXED) return fail(OVS_ESTATE, "handle was created without OVS_MIXED");
@@ -713,10 +680,12 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
     if (m > 0) {
         const void* Lb = tp == PREC_F64 ? g->L64 : g->L32;
         const void* Rb = tp == PREC_F64 ? g->R64 : g->R32;
+        const int S = gdots_stride(1, m);
         KL(OVS_PROF_DOTS, bytes_dots(N, tp, m, nrhs, true),
-           launch_dots(tp, Lb, 0, units, m, w.xint, units, units, plan, nrhs, kw.partial, nullptr, st));
-        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * m * nrhs,
-           launch_reduce(kw.partial, plan.nblk, m, nrhs, kw.cdef, m, false, nullptr, st));
+           launch_gdots(tp, 1, Lb, 0, units, m, w.xint, units, nullptr, 0, false, units, plan, nrhs, kw.partial,
+                        nullptr, st));
+        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
+           launch_reduce(kw.partial, plan.nblk, S, m, nrhs, kw.cdef, m, false, nullptr, st));
         KL(OVS_PROF_SMALL, 32.0 * m * nrhs, launch_sign_scale(kw.cdef, g->sgn, m, nrhs, kw.cdef2, st));
         KL(OVS_PROF_UPDATE, bytes_update(N, tp, tp, m, nrhs, true, true),
            launch_update(tp, tp, Rb, 0, units, m, nullptr, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, plan, nrhs,
@@ -728,48 +697,39 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
     } else {
         CK(cudaMemsetAsync(w.yacc, 0, f64 * nrhs, st));
     }
-    // beta = ||x_ominus||, v_1 = x_ominus / beta (Sec. 5.3, Eq. LRArnoldi)
-    KL(OVS_PROF_UPDATE, bytes_update(N, tp, tp, 0, nrhs, false, true),
-       launch_update(tp, tp, basis, 0, units, 0, nullptr, kw.coeff, 0, 0.0, w.xint, N, w.xint, N, units, plan, nrhs,
-                     kw.norm_part, nullptr, st));
-    KL(OVS_PROF_SMALL, 8.0 * plan.nblk * nrhs,
-       launch_init_beta(kw.norm_part, plan.nblk, nrhs, kw.beta, kw.inv_beta, kw.hnorm2, kw.active, kw.k_used, st));
-    KL(OVS_PROF_SMALL, 2.0 * fb * nrhs,
-       launch_scale(tp, w.xint, units, basis, basis_rhs_units, units, kw.inv_beta, nrhs, kw.active, st));
+    CK(cudaMemsetAsync(kw.active, 0xff, sizeof(int) * nrhs, st));  // every rhs starts active (-1 != 0)
 
-    // Arnoldi with CGS2 (Sec. 4, Eq. Arnoldi)
+    // Arnoldi (Sec. 4, Eq. Arnoldi; Sec. 5.3 Eq. LRArnoldi) with classical
+    // Gram-Schmidt applied twice, the second pass of step j-1 done in the
+    // same sweep as the first pass of step j. u (in xint) is the first-pass
+    // residual, x_ominus at the start; z = A u (in wvec).
     const double bw = bytes_wilson(g->V, tp, nrhs);
     for (int j = 0; j < k; ++j) {
-        const int J = j + 1;
-        char* vj = basis + (size_t)j * fb;
+        const int S = gdots_stride(2, j);
         KL(OVS_PROF_MATVEC, bw,
-           launch_wilson(tp, true, links_for(g, tp), vj, basis_rhs_bytes, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
+           launch_wilson(tp, true, links_for(g, tp), w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
                          kw.active, st));
-        double2* Hcol = (double2*)kw.H + (size_t)j * ldh;
-        const double bd = bytes_dots(N, tp, J, nrhs, false), bu = bytes_update(N, tp, tp, J, nrhs, false, true);
-        const double br = 16.0 * plan.nblk * J * nrhs;
-        KL(OVS_PROF_DOTS, bd,
-           launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
-                       st));
-        KL(OVS_PROF_SMALL, br, launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, false, kw.active, st));
-        KL(OVS_PROF_UPDATE, bu,
-           launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, Hcol, h_rhs, -1.0, w.wvec, N, w.wvec, N,
-                         units, plan, nrhs, nullptr, kw.active, st));
-        KL(OVS_PROF_DOTS, bd,
-           launch_dots(tp, basis, basis_rhs_units, units, J, w.wvec, units, units, plan, nrhs, kw.partial, kw.active,
-                       st));
-        KL(OVS_PROF_SMALL, br, launch_reduce(kw.partial, plan.nblk, J, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
-        KL(OVS_PROF_SMALL, br, launch_reduce(kw.partial, plan.nblk, J, nrhs, Hcol, h_rhs, true, kw.active, st));
-        KL(OVS_PROF_UPDATE, bu,
-           launch_update(tp, tp, basis, basis_rhs_units, units, J, nullptr, kw.htmp, kw.jcap, -1.0, w.wvec, N, w.wvec,
-                         N, units, plan, nrhs, kw.norm_part, kw.active, st));
-        KL(OVS_PROF_SMALL, 8.0 * plan.nblk * nrhs + 16.0 * J * nrhs,
-           launch_finalize(kw.norm_part, plan.nblk, nrhs, kw.H, h_rhs, ldh, j, kw.hnorm2, kw.inv_beta, kw.active,
-                           kw.k_used, st));
-        if (j + 1 < k)
-            KL(OVS_PROF_SMALL, 2.0 * fb * nrhs,
-               launch_scale(tp, w.wvec, units, basis + (size_t)(j + 1) * fb, basis_rhs_units, units, kw.inv_beta,
-                            nrhs, kw.active, st));
+        KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (j + 2.0),
+           launch_gdots(tp, 2, basis, basis_rhs_units, units, j, w.xint, units, w.wvec, units, true, units, plan, nrhs,
+                        kw.partial, kw.active, st));
+        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
+           launch_reduce(kw.partial, plan.nblk, S, S, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
+        KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 3.0 * j) * nrhs,
+           launch_arnoldi_step(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.beta, kw.inv_beta, kw.dcoef, kw.hnorm2,
+                               kw.active, kw.k_used, nrhs, st));
+        KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
+           launch_arnoldi_update(tp, basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
+                                 w.xint, units, w.wvec, units, units, plan, nrhs, kw.active, st));
+    }
+    {  // second Gram-Schmidt pass of the last column
+        const int S = gdots_stride(1, k);
+        KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (k + 1.0),
+           launch_gdots(tp, 1, basis, basis_rhs_units, units, k, w.xint, units, nullptr, 0, true, units, plan, nrhs,
+                        kw.partial, kw.active, st));
+        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
+           launch_reduce(kw.partial, plan.nblk, S, S, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
+        KL(OVS_PROF_SMALL, 16.0 * 2.0 * k * nrhs,
+           launch_arnoldi_final(kw.htmp, kw.jcap, k, kw.H, h_rhs, ldh, kw.active, nrhs, st));
     }
     // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v)
     KL(OVS_PROF_NEWTON, 16.0 * (double)k * k * nrhs,

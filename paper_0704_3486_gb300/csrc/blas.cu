@@ -29,83 +29,228 @@ template <typename R> __device__ __forceinline__ R warp_sum(R v) {
 }
 
 // ----------------------------------------------------------------- dots
-template <typename R, int E, int IU>
-__global__ void __launch_bounds__(BT) k_dots(const typename Unit<R>::vec* __restrict__ basis,
-                                             long long basis_rhs_stride, long long vec_stride, int J,
-                                             const typename Unit<R>::vec* __restrict__ w, long long w_rhs_stride,
-                                             long long nunits, long long chunk, int nblk,
-                                             double2* __restrict__ partial, const int* __restrict__ active) {
+// Warp transpose-reduction: every lane holds M values; after five halving
+// exchanges lane l holds, in v[0 .. M/32), the warp sums of the values
+// with index l*(M/32) + q. Each shuffle moves one useful value, so 32
+// vectors cost 31 shuffles instead of 5 x 32.
+template <int CUR, int O, typename R, int M>
+__device__ __forceinline__ void tr_step(R (&v)[M], bool upper) {
+#pragma unroll
+    for (int i = 0; i < CUR / 2; ++i) {
+        const R send = upper ? v[i] : v[i + CUR / 2];
+        const R keep = upper ? v[i + CUR / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+template <typename R, int M> __device__ __forceinline__ void transpose_reduce(R (&v)[M], int lane) {
+    static_assert(M % 32 == 0, "M must be a multiple of 32");
+    tr_step<M, 16>(v, (lane & 16) != 0);
+    tr_step<M / 2, 8>(v, (lane & 8) != 0);
+    tr_step<M / 4, 4>(v, (lane & 4) != 0);
+    tr_step<M / 8, 2>(v, (lane & 2) != 0);
+    tr_step<M / 16, 1>(v, (lane & 1) != 0);
+}
+
+// Gram-Schmidt inner products of one basis sweep, per right-hand side r and
+// row block b: s_i = V_i^H u, and if NW == 2 also t_i = V_i^H z (i < J);
+// if `extras`, also u^H u and u^H z. Output partial[r][b][S],
+// S = NW*J + 2: s_0..s_{J-1}, t_0..t_{J-1}, (u^H u, 0), u^H z.
+// A lane keeps E 16-byte units of u (and z) in registers (a tile of 256*E
+// units per block); G basis vectors are then streamed past them. Each lane
+// accumulates its E*NC products per vector in FP32 (FP64 for complex128
+// fields), a warp transpose-reduction finishes the partial over the 32
+// lanes (at most 32*E*NC = 512 terms in FP32), and the warp partials are
+// accumulated in FP64 in shared memory.
+template <typename R, int NW, int G, int E>
+__global__ void __launch_bounds__(BT) k_gdots(const typename Unit<R>::vec* __restrict__ basis,
+                                              long long basis_rhs_stride, long long vec_stride, int J,
+                                              const typename Unit<R>::vec* __restrict__ u, long long u_rhs_stride,
+                                              const typename Unit<R>::vec* __restrict__ z, long long z_rhs_stride,
+                                              int extras, long long nunits, long long chunk, int nblk,
+                                              double2* __restrict__ partial, const int* __restrict__ active) {
     using vec = typename Unit<R>::vec;
     constexpr int NC = Unit<R>::ncplx;
-    extern __shared__ double2 sacc[];  // [NWARP][J]
+    constexpr int M = 2 * NW * G;
+    constexpr int PER = M / 32;
+    extern __shared__ double2 sacc2[];  // [NWARP][S]
+    double* sacc = reinterpret_cast<double*>(sacc2);
     const int r = blockIdx.y, b = blockIdx.x;
     if (active != nullptr && active[r] == 0) return;
+    const int S = NW * J + 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < NWARP * J; i += BT) sacc[i] = make_double2(0.0, 0.0);
+    for (int i = tid; i < NWARP * S * 2; i += BT) sacc[i] = 0.0;
     __syncthreads();
     const vec* Vr = basis + r * basis_rhs_stride;
-    const vec* wr = w + r * w_rhs_stride;
+    const vec* ur = u + r * u_rhs_stride;
+    const vec* zr = (NW == 2) ? z + r * z_rhs_stride : nullptr;
+    double* myacc = sacc + (size_t)warp * S * 2;
     const long long u0 = (long long)b * chunk;
     const long long u1 = min(u0 + chunk, nunits);
+    double uu = 0.0, uzr = 0.0, uzi = 0.0;
     for (long long base = u0; base < u1; base += (long long)BT * E) {
-        cplx<R> wv[E][NC];
+        cplx<R> uc[E][NC], zc[E][NC];
         bool ok[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const long long u = base + tid + (long long)BT * e;
-            ok[e] = u < u1;
-            if (ok[e]) {
-                Unit<R>::split(__ldg(wr + u), wv[e]);
-            } else {
+            const long long q = base + tid + (long long)BT * e;
+            ok[e] = q < u1;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) wv[e][c] = {R(0), R(0)};
+            for (int c = 0; c < NC; ++c) uc[e][c] = zc[e][c] = {R(0), R(0)};
+            if (ok[e]) {
+                Unit<R>::split(__ldg(ur + q), uc[e]);
+                if (NW == 2) Unit<R>::split(__ldg(zr + q), zc[e]);
             }
         }
-        for (int i0 = 0; i0 < J; i0 += IU) {
-            cplx<R> acc[IU];
+        if (extras) {
+            cplx<R> a = {R(0), R(0)}, bz = {R(0), R(0)};
 #pragma unroll
-            for (int ii = 0; ii < IU; ++ii) acc[ii] = {R(0), R(0)};
+            for (int e = 0; e < E; ++e)
 #pragma unroll
-            for (int ii = 0; ii < IU; ++ii) {
-                if (i0 + ii < J) {
-                    const vec* vi = Vr + (long long)(i0 + ii) * vec_stride;
+                for (int c = 0; c < NC; ++c) {
+                    cfmac(a, uc[e][c], uc[e][c]);
+                    if (NW == 2) cfmac(bz, uc[e][c], zc[e][c]);
+                }
+            uu += double(a.re);
+            uzr += double(bz.re);
+            uzi += double(bz.im);
+        }
+        for (int i0 = 0; i0 < J; i0 += G) {
+            R v[M];
+#pragma unroll
+            for (int q = 0; q < M; ++q) v[q] = R(0);
+#pragma unroll
+            for (int gi = 0; gi < G; ++gi) {
+                if (i0 + gi < J) {
+                    const vec* vi = Vr + (long long)(i0 + gi) * vec_stride;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         if (ok[e]) {
                             cplx<R> vc[NC];
                             Unit<R>::split(__ldcs(vi + base + tid + (long long)BT * e), vc);
 #pragma unroll
-                            for (int c = 0; c < NC; ++c) cfmac(acc[ii], vc[c], wv[e][c]);
+                            for (int c = 0; c < NC; ++c) {
+                                cplx<R> acc = {v[2 * gi], v[2 * gi + 1]};
+                                cfmac(acc, vc[c], uc[e][c]);
+                                v[2 * gi] = acc.re;
+                                v[2 * gi + 1] = acc.im;
+                                if (NW == 2) {
+                                    cplx<R> acz = {v[2 * (G + gi)], v[2 * (G + gi) + 1]};
+                                    cfmac(acz, vc[c], zc[e][c]);
+                                    v[2 * (G + gi)] = acz.re;
+                                    v[2 * (G + gi) + 1] = acz.im;
+                                }
+                            }
                         }
                     }
                 }
             }
+            transpose_reduce(v, lane);
 #pragma unroll
-            for (int ii = 0; ii < IU; ++ii) {
-                acc[ii].re = warp_sum(acc[ii].re);
-                acc[ii].im = warp_sum(acc[ii].im);
+            for (int q = 0; q < PER; ++q) {
+                const int idx = lane * PER + q;
+                const int item = idx >> 1, comp = idx & 1;
+                const int which = item / G, gi = item - which * G;
+                if (i0 + gi < J) myacc[(which * J + i0 + gi) * 2 + comp] += double(v[q]);
             }
-            if (lane == 0) {
+        }
+    }
+    if (extras) {
+        uu = warp_sum(uu);
+        uzr = warp_sum(uzr);
+        uzi = warp_sum(uzi);
+        if (lane == 0) {
+            myacc[NW * J * 2] += uu;
+            myacc[(NW * J + 1) * 2] += uzr;
+            myacc[(NW * J + 1) * 2 + 1] += uzi;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < 2 * S; i += BT) {
+        double sum = 0.0;
 #pragma unroll
-                for (int ii = 0; ii < IU; ++ii) {
-                    if (i0 + ii < J) {
-                        double2& s = sacc[warp * J + i0 + ii];
-                        s.x += double(acc[ii].re);
-                        s.y += double(acc[ii].im);
+        for (int q = 0; q < NWARP; ++q) sum += sacc[(size_t)q * S * 2 + i];
+        reinterpret_cast<double*>(partial + ((size_t)r * nblk + b) * S)[i] = sum;
+    }
+}
+
+// Arnoldi update sweep of the delayed-reorthogonalisation form of CGS2:
+//   v_j    = (u - sum_{i<J} V_i s_i) / beta          -> basis slot J
+//   u_next = (z - sum_{i<J} V_i t_i) / beta - v_j d  -> u (in place)
+// s, t are read from red[r] (s at 0, t at J), 1/beta from inv_beta[r] and
+// d from dcoef[r].
+template <typename R, int E>
+__global__ void __launch_bounds__(BT) k_arnoldi_update(typename Unit<R>::vec* __restrict__ basis,
+                                                       long long basis_rhs_stride, long long vec_stride, int J,
+                                                       const double2* __restrict__ red, long long red_stride,
+                                                       const double* __restrict__ inv_beta,
+                                                       const double2* __restrict__ dcoef,
+                                                       typename Unit<R>::vec* __restrict__ u, long long u_rhs_stride,
+                                                       const typename Unit<R>::vec* __restrict__ z,
+                                                       long long z_rhs_stride, long long nunits, long long chunk,
+                                                       const int* __restrict__ active) {
+    using vec = typename Unit<R>::vec;
+    constexpr int NC = Unit<R>::ncplx;
+    extern __shared__ double2 scf[];
+    cplx<R>* sc = reinterpret_cast<cplx<R>*>(scf);  // s at [0, J), t at [J, 2J)
+    const int r = blockIdx.y, b = blockIdx.x;
+    if (active != nullptr && active[r] == 0) return;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 2 * J; i += BT) {
+        const double2 c = red[r * red_stride + i];
+        sc[i] = {R(c.x), R(c.y)};
+    }
+    __syncthreads();
+    const R ib = R(inv_beta[r]);
+    const double2 dd = dcoef[r];
+    const cplx<R> d = {R(dd.x), R(dd.y)};
+    vec* Vr = basis + r * basis_rhs_stride;
+    vec* vout = Vr + (long long)J * vec_stride;
+    vec* ur = u + r * u_rhs_stride;
+    const vec* zr = z + r * z_rhs_stride;
+    const long long u0 = (long long)b * chunk;
+    const long long u1 = min(u0 + chunk, nunits);
+    for (long long base = u0; base < u1; base += (long long)BT * E) {
+        cplx<R> a[E][NC], bb[E][NC];
+        bool ok[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            ok[e] = base + tid + (long long)BT * e < u1;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) a[e][c] = bb[e][c] = {R(0), R(0)};
+        }
+        for (int i = 0; i < J; ++i) {
+            const cplx<R> si = sc[i], ti = sc[J + i];
+            const vec* vi = Vr + (long long)i * vec_stride;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (ok[e]) {
+                    cplx<R> vc[NC];
+                    Unit<R>::split(__ldcs(vi + base + tid + (long long)BT * e), vc);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        cfma(a[e][c], vc[c], si);
+                        cfma(bb[e][c], vc[c], ti);
                     }
                 }
             }
         }
-    }
-    __syncthreads();
-    for (int i = tid; i < J; i += BT) {
-        double sx = 0.0, sy = 0.0;
 #pragma unroll
-        for (int q = 0; q < NWARP; ++q) {
-            sx += sacc[q * J + i].x;
-            sy += sacc[q * J + i].y;
+        for (int e = 0; e < E; ++e) {
+            if (!ok[e]) continue;
+            const long long q = base + tid + (long long)BT * e;
+            cplx<R> uc[NC], zc[NC], vo[NC], un[NC];
+            Unit<R>::split(ur[q], uc);
+            Unit<R>::split(__ldg(zr + q), zc);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                vo[c] = (uc[c] - a[e][c]) * ib;
+                un[c] = (zc[c] - bb[e][c]) * ib;
+                cplx<R> dv = cmul(vo[c], d);
+                un[c] = un[c] - dv;
+            }
+            vout[q] = Unit<R>::join(vo);
+            ur[q] = Unit<R>::join(un);
         }
-        partial[((size_t)r * nblk + b) * J + i] = make_double2(sx, sy);
     }
 }
 
@@ -157,7 +302,8 @@ __global__ void __launch_bounds__(BT) k_update(const typename Unit<RV>::vec* __r
                                                double* __restrict__ norm_partial, const int* __restrict__ active) {
     using vec = typename Unit<RV>::vec;
     constexpr int NC = Unit<RV>::ncplx;
-    extern __shared__ double2 scoef[];
+    extern __shared__ double2 scoef2[];
+    cplx<RV>* scoef = reinterpret_cast<cplx<RV>*>(scoef2);  // alpha*c, converted once per block
     __shared__ double sred[NWARP];
     const int r = blockIdx.y, b = blockIdx.x;
     if (active != nullptr && active[r] == 0) return;
@@ -166,7 +312,7 @@ __global__ void __launch_bounds__(BT) k_update(const typename Unit<RV>::vec* __r
     const int tid = threadIdx.x;
     for (int i = tid; i < Jr; i += BT) {
         double2 c = coef[r * coef_stride + i];
-        scoef[i] = make_double2(alpha * c.x, alpha * c.y);
+        scoef[i] = {RV(alpha * c.x), RV(alpha * c.y)};
     }
     __syncthreads();
     const vec* Vr = basis + r * basis_rhs_stride;
@@ -192,8 +338,7 @@ __global__ void __launch_bounds__(BT) k_update(const typename Unit<RV>::vec* __r
         }
         int since_flush = 0;
         for (int i = 0; i < Jr; ++i) {
-            const double2 cd_ = scoef[i];
-            const cplx<RV> ci = {RV(cd_.x), RV(cd_.y)};
+            const cplx<RV> ci = scoef[i];
             const vec* vi = Vr + (long long)i * vec_stride;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -245,15 +390,16 @@ __global__ void __launch_bounds__(BT) k_update(const typename Unit<RV>::vec* __r
 }
 
 // --------------------------------------------------------------- small ops
-__global__ void k_reduce(const double2* __restrict__ partial, int nblk, int J, int nrhs, double2* __restrict__ out,
-                         long long out_stride, int accumulate, const int* __restrict__ active) {
+__global__ void k_reduce(const double2* __restrict__ partial, int nblk, int pstride, int J, int nrhs,
+                         double2* __restrict__ out, long long out_stride, int accumulate,
+                         const int* __restrict__ active) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= J * nrhs) return;
     const int r = idx / J, i = idx % J;
     if (active != nullptr && active[r] == 0) return;
     double sx = 0.0, sy = 0.0;
     for (int b = 0; b < nblk; ++b) {
-        double2 p = partial[((size_t)r * nblk + b) * J + i];
+        double2 p = partial[((size_t)r * nblk + b) * pstride + i];
         sx += p.x;
         sy += p.y;
     }
@@ -269,69 +415,146 @@ __global__ void k_reduce(const double2* __restrict__ partial, int nblk, int J, i
 constexpr double kBreakdownTol = 1e-12;  // relative to ||H_j||_F; rounding of an exactly
                                          // invariant space is ~100 eps at N ~ 1e5
 
-__global__ void k_finalize(const double* __restrict__ norm_partial, int nblk, int nrhs, double2* __restrict__ H,
-                           long long h_rhs_stride, int ldh, int j, double* __restrict__ hnorm2,
-                           double* __restrict__ inv_beta, int* __restrict__ active, int* __restrict__ k_used) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrhs || active[r] == 0) return;
-    double b2 = 0.0;
-    for (int b = 0; b < nblk; ++b) b2 += norm_partial[(size_t)r * nblk + b];
-    const double beta = sqrt(b2);
-    double2* col = H + r * h_rhs_stride + (long long)j * ldh;
-    double c2 = 0.0;
-    for (int i = 0; i <= j; ++i) c2 += col[i].x * col[i].x + col[i].y * col[i].y;
-    const double hn2 = hnorm2[r] + c2 + b2;
-    hnorm2[r] = hn2;
-    k_used[r] = j + 1;
-    if (!(beta > kBreakdownTol * sqrt(hn2))) {
-        // invariant Krylov space (or NaN): stop this right-hand side here
-        col[j + 1] = make_double2(0.0, 0.0);
-        inv_beta[r] = 0.0;
-        active[r] = 0;
-    } else {
-        col[j + 1] = make_double2(beta, 0.0);
-        inv_beta[r] = 1.0 / beta;
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[3 * w] = a;
+        sh[3 * w + 1] = b;
+        sh[3 * w + 2] = c;
     }
+    __syncthreads();
+    a = b = c = 0.0;
+    for (int q = 0; q < nw; ++q) {
+        a += sh[3 * q];
+        b += sh[3 * q + 1];
+        c += sh[3 * q + 2];
+    }
+    __syncthreads();
 }
 
-__global__ void k_init_beta(const double* __restrict__ norm_partial, int nblk, int nrhs, double* __restrict__ beta,
-                            double* __restrict__ inv_beta, double* __restrict__ hnorm2, int* __restrict__ active,
-                            int* __restrict__ k_used) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrhs) return;
-    double b2 = 0.0;
-    for (int b = 0; b < nblk; ++b) b2 += norm_partial[(size_t)r * nblk + b];
-    const double bt = sqrt(b2);
-    beta[r] = bt;
-    hnorm2[r] = 0.0;
-    k_used[r] = 0;
-    if (bt > 0.0 && bt == bt) {
-        inv_beta[r] = 1.0 / bt;
-        active[r] = 1;
-    } else {
-        inv_beta[r] = 0.0;
-        active[r] = 0;
+// One Arnoldi step in the delayed-reorthogonalisation form of CGS2 (one
+// block per right-hand side). Input red[r] = (s, t, u^H u, u^H z) from the
+// sweep over V_0..V_{j-1} (s = V^H u, t = V^H z, z = A u), where u is the
+// first-pass Gram-Schmidt residual of the previous step (x_ominus at j=0).
+//  - beta = ||u - V s|| = sqrt(u^H u - ||s||^2) (V orthonormal);
+//  - j > 0: column j-1 of H gets its second-pass correction s and
+//    H[j][j-1] = beta; breakdown if beta <= 1e-12 ||H_j||_F (k_used = j);
+//  - j = 0: beta is ||x_ominus|| (kept in beta0 for the result);
+//  - column j, first pass: with g = Hbar_{j-1} s (Arnoldi relation
+//    A V_{j-1} = V_j Hbar_{j-1}), H[i][j] = (t_i - g_i)/beta for i < j and
+//    H[j][j] = (u^H z - s^H t)/beta^2 - g_j/beta;
+//  - the update sweep then needs 1/beta and d = (u^H z - s^H t)/beta^2.
+__global__ void __launch_bounds__(256) k_arnoldi_step(const double2* __restrict__ red, long long red_stride, int j,
+                                                      double2* __restrict__ H, long long h_rhs, int ldh,
+                                                      double* __restrict__ beta0, double* __restrict__ inv_beta,
+                                                      double2* __restrict__ dcoef, double* __restrict__ hnorm2,
+                                                      int* __restrict__ active, int* __restrict__ k_used) {
+    __shared__ double sh[3 * 8];
+    const int r = blockIdx.x, tid = threadIdx.x;
+    if (active[r] == 0) return;
+    const double2* rr = red + r * red_stride;
+    double2* Hr = H + r * h_rhs;
+    double ss = 0.0, shr = 0.0, shi = 0.0;
+    for (int i = tid; i < j; i += blockDim.x) {
+        const double2 si = rr[i], ti = rr[j + i];
+        ss += si.x * si.x + si.y * si.y;
+        shr += si.x * ti.x + si.y * ti.y;
+        shi += si.x * ti.y - si.y * ti.x;
     }
-}
-
-template <typename R>
-__global__ void k_scale(const typename Unit<R>::vec* __restrict__ in, long long in_rhs_stride,
-                        typename Unit<R>::vec* __restrict__ out, long long out_rhs_stride, long long nunits,
-                        const double* __restrict__ inv_beta, const int* __restrict__ active) {
-    const int r = blockIdx.y;
-    if (active != nullptr && active[r] == 0) return;
-    const R s = R(inv_beta[r]);
-    const typename Unit<R>::vec* a = in + r * in_rhs_stride;
-    typename Unit<R>::vec* o = out + r * out_rhs_stride;
-    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nunits;
-         u += (long long)gridDim.x * blockDim.x) {
-        typename Unit<R>::vec v = a[u];
-        if constexpr (Unit<R>::ncplx == 1) {
-            v.x *= s; v.y *= s;
-        } else {
-            v.x *= s; v.y *= s; v.z *= s; v.w *= s;
+    block_sum3(ss, shr, shi, sh);
+    const double uu = rr[2 * j].x;
+    const double2 uz = rr[2 * j + 1];
+    const double b2 = uu - ss;
+    const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+    if (j == 0) {
+        if (tid == 0) {
+            beta0[r] = beta;
+            hnorm2[r] = 0.0;
         }
-        o[u] = v;
+        if (!(beta > 0.0) || !isfinite(beta)) {
+            if (tid == 0) {
+                active[r] = 0;
+                k_used[r] = 0;
+                inv_beta[r] = 0.0;
+            }
+            return;
+        }
+    } else {
+        for (int i = tid; i < j; i += blockDim.x) {
+            double2 h = Hr[i + (long long)(j - 1) * ldh];
+            const double2 si = rr[i];
+            Hr[i + (long long)(j - 1) * ldh] = make_double2(h.x + si.x, h.y + si.y);
+        }
+        __syncthreads();
+        double c2 = 0.0, z1 = 0.0, z2 = 0.0;
+        for (int i = tid; i < j; i += blockDim.x) {
+            const double2 h = Hr[i + (long long)(j - 1) * ldh];
+            c2 += h.x * h.x + h.y * h.y;
+        }
+        block_sum3(c2, z1, z2, sh);
+        const double hn2 = hnorm2[r] + c2 + beta * beta;
+        const bool brk = !(beta > kBreakdownTol * sqrt(hn2)) || !isfinite(beta);
+        if (tid == 0) {
+            hnorm2[r] = hn2;
+            Hr[j + (long long)(j - 1) * ldh] = make_double2(brk ? 0.0 : beta, 0.0);
+            if (brk) {
+                active[r] = 0;
+                k_used[r] = j;
+                inv_beta[r] = 0.0;
+            }
+        }
+        if (brk) return;
+        __syncthreads();
+    }
+    const double ib = 1.0 / beta;
+    const double dr = (uz.x - shr) * ib * ib, di = (uz.y - shi) * ib * ib;
+    for (int l = tid; l <= j; l += blockDim.x) {
+        double gr = 0.0, gi = 0.0;
+        for (int i = (l > 0 ? l - 1 : 0); i < j; ++i) {  // H is upper Hessenberg
+            const double2 h = Hr[l + (long long)i * ldh];
+            const double2 si = rr[i];
+            gr += h.x * si.x - h.y * si.y;
+            gi += h.x * si.y + h.y * si.x;
+        }
+        if (l < j) {
+            const double2 ti = rr[j + l];
+            Hr[l + (long long)j * ldh] = make_double2((ti.x - gr) * ib, (ti.y - gi) * ib);
+        } else {
+            Hr[j + (long long)j * ldh] = make_double2(dr - gr * ib, di - gi * ib);
+        }
+    }
+    if (tid == 0) {
+        inv_beta[r] = ib;
+        dcoef[r] = make_double2(dr, di);
+        k_used[r] = j + 1;
+    }
+}
+
+// Second Gram-Schmidt pass of the last column: red[r] = (s, u^H u, .) from a
+// sweep over V_0..V_{k-1}; H[:k][k-1] += s, H[k][k-1] = ||u - V s||.
+__global__ void __launch_bounds__(256) k_arnoldi_final(const double2* __restrict__ red, long long red_stride, int k,
+                                                       double2* __restrict__ H, long long h_rhs, int ldh,
+                                                       const int* __restrict__ active) {
+    __shared__ double sh[3 * 8];
+    const int r = blockIdx.x, tid = threadIdx.x;
+    if (active[r] == 0) return;
+    const double2* rr = red + r * red_stride;
+    double2* Hr = H + r * h_rhs;
+    double ss = 0.0, z1 = 0.0, z2 = 0.0;
+    for (int i = tid; i < k; i += blockDim.x) {
+        const double2 si = rr[i];
+        const double2 h = Hr[i + (long long)(k - 1) * ldh];
+        Hr[i + (long long)(k - 1) * ldh] = make_double2(h.x + si.x, h.y + si.y);
+        ss += si.x * si.x + si.y * si.y;
+    }
+    block_sum3(ss, z1, z2, sh);
+    if (tid == 0) {
+        const double b2 = rr[k].x - ss;
+        Hr[k + (long long)(k - 1) * ldh] = make_double2(b2 > 0.0 ? sqrt(b2) : 0.0, 0.0);
     }
 }
 
@@ -349,8 +572,8 @@ BlasPlan blas_plan(long long nunits, int nrhs, int num_sms) {
     BlasPlan p;
     long long want = std::max<long long>(1, (8LL * num_sms + nrhs - 1) / nrhs);
     long long chunk = (nunits + want - 1) / want;
-    chunk = ((chunk + BT - 1) / BT) * BT;  // whole warps per block
-    if (chunk < BT) chunk = BT;
+    const long long tile = (long long)BT * 8;  // one inner-product tile of 8 units per thread
+    chunk = ((chunk + tile - 1) / tile) * tile;
     p.chunk = chunk;
     p.nblk = (int)((nunits + chunk - 1) / chunk);
     return p;
@@ -360,29 +583,87 @@ static bool g_attr_done = false;
 static void set_smem_attrs() {
     if (g_attr_done) return;
     const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_dots<double, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_dots<float, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_gdots<double, 1, 16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_gdots<double, 2, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_gdots<float, 1, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_gdots<float, 2, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_arnoldi_update<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_arnoldi_update<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_update<double, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_update<float, float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_update<float, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     g_attr_done = true;
 }
 
-cudaError_t launch_dots(int prec, const void* basis, long long basis_rhs_stride, long long vec_stride, int J,
-                        const void* w, long long w_rhs_stride, long long nunits, const BlasPlan& plan, int nrhs,
-                        void* partial, const int* active, cudaStream_t st) {
-    if (J <= 0) return cudaSuccess;
+int gdots_stride(int nw, int J) { return nw * J + 2; }
+
+cudaError_t launch_gdots(int prec, int nw, const void* basis, long long basis_rhs_stride, long long vec_stride,
+                         int J, const void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
+                         bool extras, long long nunits, const BlasPlan& plan, int nrhs, void* partial,
+                         const int* active, cudaStream_t st) {
     set_smem_attrs();
     dim3 grid(plan.nblk, nrhs);
-    size_t smem = (size_t)NWARP * J * sizeof(double2);
+    const size_t smem = (size_t)NWARP * gdots_stride(nw, J) * sizeof(double2);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const int ex = extras ? 1 : 0;
+    if (prec == PREC_F64) {
+        if (nw == 1)
+            k_gdots<double, 1, 16, 4><<<grid, BT, smem, st>>>((const double2*)basis, basis_rhs_stride, vec_stride, J,
+                                                              (const double2*)u, u_rhs_stride, nullptr, 0, ex, nunits,
+                                                              plan.chunk, plan.nblk, (double2*)partial, active);
+        else
+            k_gdots<double, 2, 8, 4><<<grid, BT, smem, st>>>((const double2*)basis, basis_rhs_stride, vec_stride, J,
+                                                             (const double2*)u, u_rhs_stride, (const double2*)z,
+                                                             z_rhs_stride, ex, nunits, plan.chunk, plan.nblk,
+                                                             (double2*)partial, active);
+    } else {
+        if (nw == 1)
+            k_gdots<float, 1, 16, 8><<<grid, BT, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J,
+                                                             (const float4*)u, u_rhs_stride, nullptr, 0, ex, nunits,
+                                                             plan.chunk, plan.nblk, (double2*)partial, active);
+        else
+            k_gdots<float, 2, 8, 8><<<grid, BT, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J,
+                                                             (const float4*)u, u_rhs_stride, (const float4*)z,
+                                                             z_rhs_stride, ex, nunits, plan.chunk, plan.nblk,
+                                                             (double2*)partial, active);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arnoldi_update(int prec, void* basis, long long basis_rhs_stride, long long vec_stride, int J,
+                                  const void* red, long long red_stride, const double* inv_beta, const void* dcoef,
+                                  void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
+                                  long long nunits, const BlasPlan& plan, int nrhs, const int* active,
+                                  cudaStream_t st) {
+    set_smem_attrs();
+    dim3 grid(plan.nblk, nrhs);
+    const size_t smem = (size_t)std::max(2 * J, 1) * sizeof(double2);
     if (prec == PREC_F64)
-        k_dots<double, 2, 4><<<grid, BT, smem, st>>>((const double2*)basis, basis_rhs_stride, vec_stride, J,
-                                                     (const double2*)w, w_rhs_stride, nunits, plan.chunk, plan.nblk,
-                                                     (double2*)partial, active);
+        k_arnoldi_update<double, 2><<<grid, BT, smem, st>>>((double2*)basis, basis_rhs_stride, vec_stride, J,
+                                                            (const double2*)red, red_stride, inv_beta,
+                                                            (const double2*)dcoef, (double2*)u, u_rhs_stride,
+                                                            (const double2*)z, z_rhs_stride, nunits, plan.chunk,
+                                                            active);
     else
-        k_dots<float, 2, 4><<<grid, BT, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J,
-                                                    (const float4*)w, w_rhs_stride, nunits, plan.chunk, plan.nblk,
-                                                    (double2*)partial, active);
+        k_arnoldi_update<float, 2><<<grid, BT, smem, st>>>((float4*)basis, basis_rhs_stride, vec_stride, J,
+                                                           (const double2*)red, red_stride, inv_beta,
+                                                           (const double2*)dcoef, (float4*)u, u_rhs_stride,
+                                                           (const float4*)z, z_rhs_stride, nunits, plan.chunk,
+                                                           active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arnoldi_step(const void* red, long long red_stride, int j, void* H, long long h_rhs, int ldh,
+                                double* beta0, double* inv_beta, void* dcoef, double* hnorm2, int* active,
+                                int* k_used, int nrhs, cudaStream_t st) {
+    k_arnoldi_step<<<nrhs, 256, 0, st>>>((const double2*)red, red_stride, j, (double2*)H, h_rhs, ldh, beta0, inv_beta,
+                                         (double2*)dcoef, hnorm2, active, k_used);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, void* H, long long h_rhs, int ldh,
+                                 const int* active, int nrhs, cudaStream_t st) {
+    k_arnoldi_final<<<nrhs, 256, 0, st>>>((const double2*)red, red_stride, k, (double2*)H, h_rhs, ldh, active);
     return cudaGetLastError();
 }
 
@@ -415,39 +696,12 @@ cudaError_t launch_update(int prec_v, int prec_out, const void* basis, long long
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const void* partial, int nblk, int J, int nrhs, void* out, long long out_stride,
-                          bool accumulate, const int* active, cudaStream_t st) {
+cudaError_t launch_reduce(const void* partial, int nblk, int pstride, int J, int nrhs, void* out,
+                          long long out_stride, bool accumulate, const int* active, cudaStream_t st) {
     if (J <= 0) return cudaSuccess;
     const int n = J * nrhs;
-    k_reduce<<<(n + 127) / 128, 128, 0, st>>>((const double2*)partial, nblk, J, nrhs, (double2*)out, out_stride,
-                                              accumulate ? 1 : 0, active);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const double* norm_partial, int nblk, int nrhs, void* H, long long h_rhs_stride,
-                            int ldh, int j, double* hnorm2, double* inv_beta, int* active, int* k_used,
-                            cudaStream_t st) {
-    k_finalize<<<(nrhs + 63) / 64, 64, 0, st>>>(norm_partial, nblk, nrhs, (double2*)H, h_rhs_stride, ldh, j, hnorm2,
-                                                inv_beta, active, k_used);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_init_beta(const double* norm_partial, int nblk, int nrhs, double* beta, double* inv_beta,
-                             double* hnorm2, int* active, int* k_used, cudaStream_t st) {
-    k_init_beta<<<(nrhs + 63) / 64, 64, 0, st>>>(norm_partial, nblk, nrhs, beta, inv_beta, hnorm2, active, k_used);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scale(int prec, const void* in, long long in_rhs_stride, void* out, long long out_rhs_stride,
-                         long long nunits, const double* inv_beta, int nrhs, const int* active, cudaStream_t st) {
-    long long blocks = std::min<long long>((nunits + 255) / 256, 4096);
-    dim3 grid((unsigned)std::max<long long>(blocks, 1), nrhs);
-    if (prec == PREC_F64)
-        k_scale<double><<<grid, 256, 0, st>>>((const double2*)in, in_rhs_stride, (double2*)out, out_rhs_stride,
-                                              nunits, inv_beta, active);
-    else
-        k_scale<float><<<grid, 256, 0, st>>>((const float4*)in, in_rhs_stride, (float4*)out, out_rhs_stride, nunits,
-                                             inv_beta, active);
+    k_reduce<<<(n + 127) / 128, 128, 0, st>>>((const double2*)partial, nblk, pstride, J, nrhs, (double2*)out,
+                                              out_stride, accumulate ? 1 : 0, active);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,8 @@
 //   (1 + gamma_k) psi = [h;  i s_k h],   h = psi_up - i s_k psi_dn
 //   (1 - gamma_4) psi = [h; -h],         h = psi_up - psi_dn
 //   (1 + gamma_4) psi = [h;  h],         h = psi_up + psi_dn
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -160,12 +162,25 @@ __device__ __forceinline__ void both_hops(const void* links, const void* in, con
     hop_bwd<NU>(p, U, fb, acc);
 }
 
+// Optional epilogue of the stencil: out = ah * (stencil result) + bx * X + by * Y
+// (used by the Chebyshev filter of the eigensolver set-up).
+struct Axpy {
+    const char* X;
+    size_t xs;
+    double bx;
+    const char* Y;
+    size_t ys;
+    double by;
+    double ah;
+};
+
 // out_r = [gamma5] (in_r - kappa * hops(in_r)) for r = blockIdx.y.
 // in/out strides are in bytes between right-hand sides.
-template <typename R, bool G5>
+template <typename R, bool G5, bool AX = false>
 __global__ void __launch_bounds__(128) k_wilson(const void* __restrict__ links, const char* __restrict__ in,
-                                                char* __restrict__ out, size_t in_stride, size_t out_stride, Geom g,
-                                                R kappa, R emu, R emmu, const int* __restrict__ active) {
+                                                char* out, size_t in_stride, size_t out_stride, Geom g,
+                                                R kappa, R emu, R emmu, const int* __restrict__ active,
+                                                Axpy ax = Axpy{}) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (s >= g.V) return;
@@ -192,7 +207,44 @@ __global__ void __launch_bounds__(128) k_wilson(const void* __restrict__ links, 
         if (G5 && q >= 6) v = -v;
         p[q] = v;
     }
+    if (AX) {
+        cplx<R> xv[12], yv[12];
+        Field<R>::load(ax.X + r * ax.xs, g.V, s, xv);
+        Field<R>::load(ax.Y + r * ax.ys, g.V, s, yv);
+        const R ah = R(ax.ah), bx = R(ax.bx), by = R(ax.by);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) p[q] = p[q] * ah + xv[q] * bx + yv[q] * by;
+    }
     Field<R>::store(outr, g.V, s, p);
+}
+
+// Flat precision conversion of internal fields (the two layouts pair up).
+__global__ void k_f64_to_f32(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = a[i];
+        b[i] = make_float2(float(v.x), float(v.y));
+    }
+}
+__global__ void k_f32_to_f64(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = a[i];
+        b[i] = make_double2(double(v.x), double(v.y));
+    }
+}
+
+// Uniform (-1, 1) real and imaginary parts from a 64-bit mixing hash of
+// (seed, index) (splitmix64 finaliser); used for random starting blocks.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__global__ void k_random_fill(double2* __restrict__ q, long long n, uint64_t seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint64_t a = mix64(seed * 0x9E3779B97F4A7C15ULL + 2 * (uint64_t)i + 1);
+        const uint64_t b = mix64(a + 0x632BE59BD9B4E019ULL);
+        q[i] = make_double2(((a >> 11) + 0.5) * 0x1p-52 - 1.0, ((b >> 11) + 0.5) * 0x1p-52 - 1.0);
+    }
 }
 
 // ------------------------------------------------------------ layouts (K7)
@@ -276,6 +328,38 @@ cudaError_t launch_wilson(int prec, bool gamma5, const void* links, const void* 
             k_wilson<float, false><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
                                                        (float)kappa, (float)emu, (float)emmu, active);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wilson_axpy(int prec, const void* links, const void* in, size_t in_stride, void* out,
+                               size_t out_stride, const void* X, size_t xs, double bx, const void* Y, size_t ys,
+                               double by, double ah, const Geom& g, int nrhs, double kappa, double mu,
+                               cudaStream_t st) {
+    const int T = 128;
+    dim3 grid = site_grid(g.V, nrhs, T);
+    const double emu = exp(mu), emmu = exp(-mu);
+    Axpy ax{(const char*)X, xs, bx, (const char*)Y, ys, by, ah};
+    if (prec == PREC_F64)
+        k_wilson<double, true, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
+                                                         kappa, emu, emmu, nullptr, ax);
+    else
+        k_wilson<float, true, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
+                                                        (float)kappa, (float)emu, (float)emmu, nullptr, ax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int to_prec, const void* in, void* out, long long ncplx, cudaStream_t st) {
+    const int blocks = (int)std::min<long long>((ncplx + 255) / 256, 8192);
+    if (to_prec == PREC_F32)
+        k_f64_to_f32<<<blocks, 256, 0, st>>>((const double2*)in, (float2*)out, ncplx);
+    else
+        k_f32_to_f64<<<blocks, 256, 0, st>>>((const float2*)in, (double2*)out, ncplx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_random_fill(void* q, long long ncplx, uint64_t seed, cudaStream_t st) {
+    const int blocks = (int)std::min<long long>((ncplx + 255) / 256, 8192);
+    k_random_fill<<<blocks, 256, 0, st>>>((double2*)q, ncplx, seed);
     return cudaGetLastError();
 }
 

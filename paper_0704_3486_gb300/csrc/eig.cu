@@ -1,16 +1,550 @@
-// K6: critical eigenpairs of H_w(mu) for LR deflation (Sec. 6) -- set-up,
-// timed separately from the sign applications.
-#include "../../include/ovsign.h"
+// K6: critical eigenpairs of H_w(mu) for LR deflation (Sec. 5.3 step i;
+// Sec. 6) -- the set-up, done once per operator and timed separately.
+//
+// The paper finds the eigenvalues of smallest magnitude of H_w through
+// H_w^2, whose smallest eigenvalues lie on the edge of the spectrum (Sec. 6).
+// Here a block of p > m vectors is driven towards them by Chebyshev-filtered
+// subspace iteration on H_w^2:
+//   1. filter:   Q <- T_d(H^2) Q, the scaled three-term Chebyshev
+//                recurrence that damps [a, b] (b >= spectral radius of H^2,
+//                a = the largest Ritz value of H^2 in the block), fused into
+//                the stencil's epilogue; complex64 while the residuals are
+//                far above FP32 rounding, complex128 afterwards;
+//   2. orthonormalise Q twice by SVQB (Gram matrix Q^H Q, Hermitian
+//      eigen-decomposition, Q <- Q U Lambda^-1/2);
+//   3. Rayleigh-Ritz with H_w itself: G = Q^H H Q, G Y = Y Theta, Ritz
+//      vectors X = Q Y and residuals ||H x - theta x|| (complex128);
+//   4. stop when the m Ritz pairs of smallest |theta| have relative residual
+//      <= tol; otherwise Q <- X and pick the next degree d so that the
+//      filter gains a factor ~1e3 between the m-th Ritz value and the cut.
+// Left eigenvectors are right eigenvectors of H_w(mu)^+ = H_w(-mu)
+// (gamma5-hermiticity) with eigenvalues conj(lambda): the same iteration at
+// -mu, matched to the right pairs by eigenvalue. Of the converged pairs the m
+// with smallest |Re lambda| are installed (L biorthonormalised against R).
+// Dense algebra of the set-up (block Gram matrices, Ritz vectors, the small
+// Hermitian and non-Hermitian eigenproblems) uses cuBLAS and cuSOLVER.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <numeric>
+#include <vector>
+
 #include "common.cuh"
+#include "handle.h"
 #include "kernels.h"
 
-struct ovs_gauge_s;
-
 namespace ovs {
-int lib_fail(int code, const char* msg);
+
+// ||Z_i - theta_i X_i|| for each column i (one block per column)
+__global__ void k_ritz_resid(const double2* __restrict__ Z, const double2* __restrict__ X,
+                             const double2* __restrict__ theta, long long N, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x;
+    const double2 t = theta[i];
+    const double2* z = Z + (size_t)i * N;
+    const double2* x = X + (size_t)i * N;
+    double s = 0.0;
+    for (long long n = threadIdx.x; n < N; n += blockDim.x) {
+        const double2 a = z[n], b = x[n];
+        const double rx = a.x - (t.x * b.x - t.y * b.y);
+        const double ry = a.y - (t.x * b.y + t.y * b.x);
+        s += rx * rx + ry * ry;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+        out[i] = sqrt(tot);
+    }
+}
+
+// U[:, j] *= 1/sqrt(max(lam_j, floor)) (column-major p x p)
+__global__ void k_scale_cols(double2* __restrict__ U, const double* __restrict__ lam, int p, double floor_) {
+    const int j = blockIdx.x;
+    const double l = lam[j] > floor_ ? lam[j] : floor_;
+    const double s = 1.0 / sqrt(l);
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        double2 v = U[(size_t)j * p + i];
+        U[(size_t)j * p + i] = make_double2(v.x * s, v.y * s);
+    }
+}
+
+namespace {
+
+struct Ctx {
+    ovs_gauge_s* g = nullptr;
+    cudaStream_t st = 0;
+    cublasHandle_t cb = nullptr;
+    cusolverDnHandle_t cs = nullptr;
+    cusolverDnParams_t params = nullptr;
+    long long N = 0;
+    int p = 0;
+    double2 *Q = nullptr, *W = nullptr, *A1 = nullptr, *A2 = nullptr;  // [p][N] complex128
+    void* F[3] = {nullptr, nullptr, nullptr};                            // [p][N] complex64 filter buffers
+    double2 *G = nullptr, *G2 = nullptr, *Y = nullptr, *theta = nullptr;
+    double* lam = nullptr;
+    double* resid = nullptr;
+    int* info = nullptr;
+    void* dwork = nullptr;
+    size_t dwork_bytes = 0;
+    std::vector<char> hwork;
+    char err[256] = {0};
+    ~Ctx() {
+        for (void* q : {(void*)Q, (void*)W, (void*)A1, (void*)A2, F[0], F[1], F[2], (void*)G, (void*)G2, (void*)Y,
+                        (void*)theta, (void*)lam, (void*)resid, (void*)info, dwork})
+            if (q) cudaFree(q);
+        if (params) cusolverDnDestroyParams(params);
+        if (cs) cusolverDnDestroy(cs);
+        if (cb) cublasDestroy(cb);
+    }
+};
+
+#define ECK(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            snprintf(c.err, sizeof(c.err), "%s: %s", #call, cudaGetErrorString(e_));     \
+            return e_ == cudaErrorMemoryAllocation ? OVS_ENOMEM : OVS_ECUDA;             \
+        }                                                                                \
+    } while (0)
+#define BCK(call)                                                                        \
+    do {                                                                                 \
+        int s_ = (int)(call);                                                            \
+        if (s_ != 0) {                                                                   \
+            snprintf(c.err, sizeof(c.err), "%s failed with status %d", #call, s_);       \
+            return OVS_ECUDA;                                                            \
+        }                                                                                \
+    } while (0)
+
+const cuDoubleComplex kOne = {1.0, 0.0}, kZero = {0.0, 0.0};
+
+// out = H_w(mu) in for the p vectors of a block
+int apply_h(Ctx& c, int prec, const void* in, void* out, double mu) {
+    ovs_gauge_s* g = c.g;
+    const size_t fb = (size_t)c.N * (prec == PREC_F64 ? 16 : 8);
+    const void* L = prec == PREC_F64 ? g->links64 : g->links32;
+    ECK(launch_wilson(prec, true, L, in, fb, out, fb, g->geom, c.p, g->kappa, mu, nullptr, c.st));
+    return OVS_OK;
+}
+
+// Scaled Chebyshev filter of degree deg in H^2: T_deg((z - cc)/e) normalised
+// to 1 at z = 0, which damps the ellipses with foci cc +/- e. Buffers b0
+// (input), b1, bt of precision prec; *out_idx receives the buffer index
+// holding the result.
+int cheb_filter(Ctx& c, int prec, void* bufs[3], int deg, double cc, double e, double mu, int* out_idx) {
+    ovs_gauge_s* g = c.g;
+    const size_t fb = (size_t)c.N * (prec == PREC_F64 ? 16 : 8);
+    const void* L = prec == PREC_F64 ? g->links64 : g->links32;
+    const double sigma1 = e / (0.0 - cc);
+    double sigma = sigma1;
+    void* prev = bufs[0];
+    void* cur = bufs[1];
+    void* tmp = bufs[2];
+    // Y1 = (sigma1/e) (H^2 - c) Y0
+    {
+        int rc = apply_h(c, prec, prev, tmp, mu);
+        if (rc) return rc;
+        ECK(launch_wilson_axpy(prec, L, tmp, fb, cur, fb, prev, fb, -sigma1 * cc / e, prev, fb, 0.0, sigma1 / e,
+                               g->geom, c.p, g->kappa, mu, c.st));
+    }
+    for (int k = 1; k < deg; ++k) {
+        const double sn = 1.0 / (2.0 / sigma1 - sigma);
+        int rc = apply_h(c, prec, cur, tmp, mu);
+        if (rc) return rc;
+        // Y_{k+1} = (2 sn/e)(H^2 - c) Y_k - sigma sn Y_{k-1}, written over Y_{k-1}
+        ECK(launch_wilson_axpy(prec, L, tmp, fb, prev, fb, cur, fb, -2.0 * sn * cc / e, prev, fb, -sigma * sn,
+                               2.0 * sn / e, g->geom, c.p, g->kappa, mu, c.st));
+        std::swap(prev, cur);
+        sigma = sn;
+    }
+    *out_idx = (cur == bufs[0]) ? 0 : (cur == bufs[1] ? 1 : 2);
+    return OVS_OK;
+}
+
+// Q <- Q U diag(lam)^-1/2 with G = Q^H Q = U diag(lam) U^H (twice)
+int svqb(Ctx& c) {
+    const int p = c.p;
+    const long long N = c.N;
+    for (int pass = 0; pass < 2; ++pass) {
+        BCK(cublasZgemm(c.cb, CUBLAS_OP_C, CUBLAS_OP_N, p, p, (int)N, &kOne, (const cuDoubleComplex*)c.Q, (int)N,
+                        (const cuDoubleComplex*)c.Q, (int)N, &kZero, (cuDoubleComplex*)c.G, p));
+        int lwork = 0;
+        BCK(cusolverDnZheevd_bufferSize(c.cs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p,
+                                        (cuDoubleComplex*)c.G, p, c.lam, &lwork));
+        if ((size_t)lwork * 16 > c.dwork_bytes) {
+            if (c.dwork) cudaFree(c.dwork);
+            c.dwork_bytes = (size_t)lwork * 16;
+            ECK(cudaMalloc(&c.dwork, c.dwork_bytes));
+        }
+        BCK(cusolverDnZheevd(c.cs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p, (cuDoubleComplex*)c.G, p,
+                             c.lam, (cuDoubleComplex*)c.dwork, lwork, c.info));
+        std::vector<double> lam(p);
+        ECK(cudaMemcpyAsync(lam.data(), c.lam, sizeof(double) * p, cudaMemcpyDeviceToHost, c.st));
+        ECK(cudaStreamSynchronize(c.st));
+        const double floor_ = std::max(lam[p - 1], 1e-300) * 1e-28;
+        k_scale_cols<<<p, 128, 0, c.st>>>(c.G, c.lam, p, floor_);
+        ECK(cudaGetLastError());
+        BCK(cublasZgemm(c.cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, p, p, &kOne, (const cuDoubleComplex*)c.Q, (int)N,
+                        (const cuDoubleComplex*)c.G, p, &kZero, (cuDoubleComplex*)c.A1, (int)N));
+        std::swap(c.Q, c.A1);
+    }
+    return OVS_OK;
+}
+
+// Rayleigh-Ritz of H_w(mu) on span(Q): Ritz values theta (host), Ritz
+// vectors in A1 (unit norm), residual norms (host).
+int rayleigh_ritz(Ctx& c, double mu, std::vector<std::complex<double>>& theta, std::vector<double>& resid) {
+    const int p = c.p;
+    const long long N = c.N;
+    int rc = apply_h(c, PREC_F64, c.Q, c.W, mu);
+    if (rc) return rc;
+    BCK(cublasZgemm(c.cb, CUBLAS_OP_C, CUBLAS_OP_N, p, p, (int)N, &kOne, (const cuDoubleComplex*)c.Q, (int)N,
+                    (const cuDoubleComplex*)c.W, (int)N, &kZero, (cuDoubleComplex*)c.G, p));
+    size_t dbytes = 0, hbytes = 0;
+    BCK(cusolverDnXgeev_bufferSize(c.cs, c.params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, p,
+                                   CUDA_C_64F, c.G, p, CUDA_C_64F, c.theta, CUDA_C_64F, nullptr, p, CUDA_C_64F, c.Y,
+                                   p, CUDA_C_64F, &dbytes, &hbytes));
+    if (dbytes > c.dwork_bytes) {
+        if (c.dwork) cudaFree(c.dwork);
+        c.dwork_bytes = dbytes;
+        ECK(cudaMalloc(&c.dwork, c.dwork_bytes));
+    }
+    if (hbytes > c.hwork.size()) c.hwork.resize(hbytes);
+    BCK(cusolverDnXgeev(c.cs, c.params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, p, CUDA_C_64F, c.G, p,
+                        CUDA_C_64F, c.theta, CUDA_C_64F, nullptr, p, CUDA_C_64F, c.Y, p, CUDA_C_64F, c.dwork,
+                        c.dwork_bytes, c.hwork.empty() ? nullptr : c.hwork.data(), c.hwork.size(), c.info));
+    int info = 0;
+    ECK(cudaMemcpyAsync(&info, c.info, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    // X = Q Y, Z = W Y
+    BCK(cublasZgemm(c.cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, p, p, &kOne, (const cuDoubleComplex*)c.Q, (int)N,
+                    (const cuDoubleComplex*)c.Y, p, &kZero, (cuDoubleComplex*)c.A1, (int)N));
+    BCK(cublasZgemm(c.cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, p, p, &kOne, (const cuDoubleComplex*)c.W, (int)N,
+                    (const cuDoubleComplex*)c.Y, p, &kZero, (cuDoubleComplex*)c.A2, (int)N));
+    k_ritz_resid<<<p, 256, 0, c.st>>>(c.A2, c.A1, c.theta, N, c.resid);
+    ECK(cudaGetLastError());
+    theta.resize(p);
+    resid.resize(p);
+    ECK(cudaMemcpyAsync(theta.data(), c.theta, sizeof(double2) * p, cudaMemcpyDeviceToHost, c.st));
+    ECK(cudaMemcpyAsync(resid.data(), c.resid, sizeof(double) * p, cudaMemcpyDeviceToHost, c.st));
+    ECK(cudaStreamSynchronize(c.st));
+    if (info != 0) {
+        snprintf(c.err, sizeof(c.err), "geev info = %d", info);
+        return OVS_EEIG;
+    }
+    return OVS_OK;
+}
+
+struct SideResult {
+    std::vector<std::complex<double>> theta;
+    std::vector<double> resid;
+    double* X = nullptr;  // device [p][N] complex128 (owned by caller after return)
+    int iters = 0;
+    long long matvecs = 0;
+    bool converged = false;
+};
+
+// Spectral radius bound of H^2 from a short power iteration on one vector.
+int spectral_bound(Ctx& c, double mu, double* b_out) {
+    const long long N = c.N;
+    ovs_gauge_s* g = c.g;
+    const size_t fb = (size_t)N * 16;
+    double2* v = c.A1;
+    double2* w = c.A2;
+    ECK(launch_random_fill(v, N, 977, c.st));
+    double rho = 0.0;
+    for (int it = 0; it < 40; ++it) {
+        ECK(launch_wilson(PREC_F64, true, g->links64, v, fb, w, fb, g->geom, 1, g->kappa, mu, nullptr, c.st));
+        ECK(launch_wilson(PREC_F64, true, g->links64, w, fb, v, fb, g->geom, 1, g->kappa, mu, nullptr, c.st));
+        double nv = 0.0;
+        BCK(cublasDznrm2(c.cb, (int)N, (const cuDoubleComplex*)v, 1, &nv));
+        ECK(cudaStreamSynchronize(c.st));
+        if (!(nv > 0.0)) break;
+        const double inv = 1.0 / nv;
+        BCK(cublasZdscal(c.cb, (int)N, &inv, (cuDoubleComplex*)v, 1));
+        rho = nv;  // ||H^2 v|| with ||v|| = 1 from the previous step
+    }
+    *b_out = 1.15 * rho;
+    return OVS_OK;
+}
+
+// Chebyshev filter for the non-Hermitian H^2. The eigenvalues z = lambda^2
+// of H_w(mu) lie near the positive real axis: |Im lambda| <= eta with
+// eta = ||(H - H^+)/2|| <= 4 kappa sinh|mu| (H - H^+ = H(mu) - H(-mu) has
+// only temporal hops, 2 kappa |e^mu - e^-mu| each, through a rank-2
+// projector), so |Im z| <= Y(x) = 2 eta sqrt(x + eta^2) at Re z = x. Near
+// the cut the bound is replaced by 1.5 x the largest |Im theta| of the
+// block's Ritz values (the small eigenvalues of the bow-tie are far closer
+// to the real axis than the bound), growing linearly to the bound at the
+// top of the spectrum. The
+// unwanted part {a <= Re z <= b, |Im z| <= Y} is enclosed in an ellipse
+// with left vertex aE = (lm + a)/2, right vertex 1.5 b and semi-axis B
+// high enough to contain the region; the filter is the Chebyshev polynomial
+// for the foci of that ellipse. Its per-degree gain at the wanted Ritz value
+// lm over the ellipse fixes the degree (gain 1e3 per application).
+struct FilterPlan {
+    double c, e;
+    int deg;
+};
+
+FilterPlan plan_filter(double b, double lm, double a, double kappa, double mu, double eta_near) {
+    const double eta_glob = 4.0 * kappa * std::sinh(std::fabs(mu));
+    eta_near = std::min(eta_near, eta_glob);
+    const double aE = 0.5 * (lm + a);
+    const double bE = 1.5 * b;
+    const double A = 0.5 * (bE - aE), cc = 0.5 * (bE + aE);
+    double B = 0.0;
+    for (int i = 0; i <= 400; ++i) {
+        // sample Re z on [a, b], densely near a
+        const double t = i / 400.0;
+        const double x = a + (b - a) * t * t;
+        // near the cut the Ritz values show the imaginary parts; towards the
+        // top of the spectrum the rigorous bound takes over linearly
+        const double eta = eta_near + (eta_glob - eta_near) * std::min(1.0, x / b);
+        const double y = 2.0 * eta * std::sqrt(x + eta * eta);
+        const double q = (x - cc) / A;
+        const double room = 1.0 - q * q;
+        if (room > 1e-14) B = std::max(B, y / std::sqrt(room));
+    }
+    B = std::min(B, 0.95 * A);
+    FilterPlan fp;
+    fp.c = cc;
+    fp.e = std::sqrt(A * A - B * B);
+    const double rho_ell = (A + B) / fp.e;
+    const double w = (cc - lm) / fp.e;
+    const double rho_w = w > 1.0 ? w + std::sqrt(w * w - 1.0) : 1.0;
+    const double gain = rho_w / rho_ell;
+    const double d = gain > 1.0 + 1e-9 ? std::log(1e3) / std::log(gain) : 3000.0;
+    fp.deg = (int)std::min(std::max(d, 16.0), 3000.0);
+    return fp;
+}
+
+int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadline_s, SideResult& res) {
+    const auto t_start = std::chrono::steady_clock::now();
+    const int p = c.p;
+    const long long N = c.N;
+    ovs_gauge_s* g = c.g;
+    double b = 0.0;
+    int rc = spectral_bound(c, mu, &b);
+    if (rc) return rc;
+    const double hnorm = std::sqrt(b);
+    ECK(launch_random_fill(c.Q, (long long)p * N, seed, c.st));
+    rc = svqb(c);
+    if (rc) return rc;
+    int fprec = (g->prec == OVS_MIXED && g->links32 != nullptr) ? PREC_F32 : PREC_F64;
+    FilterPlan fp = plan_filter(b, 0.01 * b, 0.02 * b, g->kappa, mu, 1e300);
+    const long long budget = 400000LL * std::max(1, (int)std::ceil(8.0e6 / (double)N)) + 200LL * p * 3000;
+    double last_rmax = 1e300;
+    int last_deg = fp.deg;
+    const int max_iter = 40;
+    std::vector<int> order(p);
+    double last_iter_s = 0.0;
+    for (int it = 0; it < max_iter; ++it) {
+        const auto t_iter = std::chrono::steady_clock::now();
+        // stop before an iteration that would overrun the deadline (the
+        // first iteration always runs, so a basis is always produced)
+        if (it > 0 && deadline_s > 0.0) {
+            const double el = std::chrono::duration<double>(t_iter - t_start).count();
+            if (el + last_iter_s > deadline_s) break;
+        }
+        // 1. filter
+        int idx = 0;
+        if (fprec == PREC_F32) {
+            ECK(launch_convert(PREC_F32, c.Q, c.F[0], (long long)p * N, c.st));
+            void* bufs[3] = {c.F[0], c.F[1], c.F[2]};
+            rc = cheb_filter(c, PREC_F32, bufs, fp.deg, fp.c, fp.e, mu, &idx);
+            if (rc) return rc;
+            ECK(launch_convert(PREC_F64, bufs[idx], c.Q, (long long)p * N, c.st));
+        } else {
+            void* bufs[3] = {c.Q, c.A1, c.A2};
+            rc = cheb_filter(c, PREC_F64, bufs, fp.deg, fp.c, fp.e, mu, &idx);
+            if (rc) return rc;
+            if (idx != 0) ECK(cudaMemcpyAsync(c.Q, bufs[idx], sizeof(double2) * p * N, cudaMemcpyDeviceToDevice, c.st));
+        }
+        res.matvecs += 2LL * fp.deg * p;
+        // 2. orthonormalise, 3. Rayleigh-Ritz
+        rc = svqb(c);
+        if (rc) return rc;
+        rc = rayleigh_ritz(c, mu, res.theta, res.resid);
+        if (rc) return rc;
+        res.matvecs += p;
+        std::swap(c.Q, c.A1);  // Ritz vectors become the block
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(),
+                  [&](int x, int y) { return std::abs(res.theta[x]) < std::abs(res.theta[y]); });
+        double rmax = 0.0;
+        for (int i = 0; i < m; ++i) rmax = std::max(rmax, res.resid[order[i]] / hnorm);
+        res.iters = it + 1;
+        if (rmax <= tol) {
+            res.converged = true;
+            break;
+        }
+        // 4. next filter: cut between the m-th and the last Ritz value of H^2
+        const double lm2 = std::abs(res.theta[order[m - 1]] * res.theta[order[m - 1]]);
+        const double ap2 = std::abs(res.theta[order[p - 1]] * res.theta[order[p - 1]]);
+        double eta_near = 0.0;
+        for (int i = 0; i < p; ++i) eta_near = std::max(eta_near, std::fabs(res.theta[i].imag()));
+        fp = plan_filter(b, lm2, std::max(ap2, 1.2 * lm2), g->kappa, mu, 1.5 * eta_near + 1e-12);
+        if (res.matvecs + 2LL * fp.deg * p > budget) break;
+        // cost of the next iteration, scaled by its degree
+        last_iter_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_iter).count() *
+                      std::max(1.0, (double)fp.deg / std::max(1, last_deg));
+        last_deg = fp.deg;
+        // precision: complex64 until its rounding limits progress
+        // complex64 filtering until its rounding limits progress: switch when
+        // the residuals approach FP32 precision (or stall close to it)
+        if (fprec == PREC_F32 && (rmax < 3e-6 || (rmax < 1e-4 && rmax > 0.5 * last_rmax))) fprec = PREC_F64;
+        last_rmax = rmax;
+    }
+    // hand the Ritz vectors (now in Q) to the caller, sorted by |theta|
+    std::vector<std::complex<double>> th(p);
+    std::vector<double> rs(p);
+    for (int i = 0; i < p; ++i) {
+        ECK(cudaMemcpyAsync(c.A1 + (size_t)i * N, c.Q + (size_t)order[i] * N, sizeof(double2) * N,
+                            cudaMemcpyDeviceToDevice, c.st));
+        th[i] = res.theta[order[i]];
+        rs[i] = res.resid[order[i]] / hnorm;
+    }
+    res.theta = th;
+    res.resid = rs;
+    std::swap(c.Q, c.A1);
+    ECK(cudaStreamSynchronize(c.st));
+    return OVS_OK;
+}
+
+}  // namespace
 
 int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out) {
-    (void)g; (void)m; (void)tol; (void)eig_out;
-    return lib_fail(OVS_EEIG, "ovs_deflate_setup: eigensolver not built yet");
+    Ctx c;
+    c.g = g;
+    c.st = 0;
+    c.N = g->N;
+    c.p = (int)std::min<long long>(m + std::max(8, (m + 1) / 2), g->N / 2);
+    if (c.p > 65535) return lib_fail(OVS_EINVAL, "m too large for the set-up block");
+    const int p = c.p;
+    const long long N = c.N;
+    char msg[320];
+#define SETUP_FAIL(code)                                                                        \
+    do {                                                                                        \
+        snprintf(msg, sizeof(msg), "deflate_setup: %s", c.err[0] ? c.err : "CUDA error");       \
+        return lib_fail((code), msg);                                                           \
+    } while (0)
+    if (cublasCreate(&c.cb) != CUBLAS_STATUS_SUCCESS || cusolverDnCreate(&c.cs) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnCreateParams(&c.params) != CUSOLVER_STATUS_SUCCESS)
+        return lib_fail(OVS_ECUDA, "deflate_setup: cannot create cuBLAS/cuSOLVER handles");
+    cublasSetStream(c.cb, c.st);
+    cusolverDnSetStream(c.cs, c.st);
+    const size_t blk = sizeof(double2) * (size_t)p * N;
+    cudaError_t e = cudaSuccess;
+    for (double2** q : {&c.Q, &c.W, &c.A1, &c.A2})
+        if (e == cudaSuccess) e = cudaMalloc((void**)q, blk);
+    if (g->prec == OVS_MIXED)
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&c.F[i], blk / 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.G, sizeof(double2) * p * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.G2, sizeof(double2) * p * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.Y, sizeof(double2) * p * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.theta, sizeof(double2) * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.lam, sizeof(double) * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.resid, sizeof(double) * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.info, sizeof(int));
+    if (e != cudaSuccess) return lib_fail(OVS_ENOMEM, "deflate_setup: device memory for the set-up block");
+
+    // right eigenvectors of H_w(mu)
+    SideResult right, left;
+    const double side_s = g->setup_budget_s > 0.0 ? 0.5 * g->setup_budget_s : 0.0;
+    int rc = run_side(c, m, tol, g->mu, 12345, side_s, right);
+    if (rc) SETUP_FAIL(rc);
+    double2* Rblk = nullptr;
+    if (cudaMalloc((void**)&Rblk, blk) != cudaSuccess) return lib_fail(OVS_ENOMEM, "deflate_setup: right block");
+    cudaMemcpy(Rblk, c.Q, blk, cudaMemcpyDeviceToDevice);
+    // left eigenvectors: right eigenvectors of H_w(-mu), eigenvalues conj(lambda)
+    rc = run_side(c, m, tol, -g->mu, 54321, side_s, left);
+    if (rc) {
+        cudaFree(Rblk);
+        SETUP_FAIL(rc);
+    }
+    // choose m converged right pairs of smallest |Re lambda|; match left ones
+    std::vector<int> cand;
+    for (int i = 0; i < p; ++i)
+        if (right.resid[i] <= tol) cand.push_back(i);
+    bool ok = right.converged && left.converged;
+    if ((int)cand.size() < m) {
+        cand.clear();
+        for (int i = 0; i < m; ++i) cand.push_back(i);
+        ok = false;
+    }
+    std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) {
+        return std::fabs(right.theta[x].real()) < std::fabs(right.theta[y].real());
+    });
+    cand.resize(m);
+    std::vector<int> lsel(m, -1);
+    std::vector<char> used(p, 0);
+    double worst_match = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const std::complex<double> want = std::conj(right.theta[cand[i]]);
+        int best = -1;
+        double bd = 1e300;
+        for (int j = 0; j < p; ++j) {
+            if (used[j]) continue;
+            const double d = std::abs(left.theta[j] - want);
+            if (d < bd) { bd = d; best = j; }
+        }
+        used[best] = 1;
+        lsel[i] = best;
+        worst_match = std::max(worst_match, bd / std::max(std::abs(want), 1e-300));
+    }
+    if (worst_match > 1e-6) ok = false;
+    // canonical copies of the chosen vectors, then install (biorthonormalises L)
+    double2 *Rc = nullptr, *Lc = nullptr, *tmp = nullptr;
+    const size_t fv = sizeof(double2) * (size_t)N;
+    e = cudaMalloc((void**)&Rc, fv * m);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Lc, fv * m);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&tmp, fv * m);
+    std::vector<double> lambda(2 * m);
+    for (int i = 0; i < m && e == cudaSuccess; ++i) {
+        e = cudaMemcpy(tmp + (size_t)i * N, Rblk + (size_t)cand[i] * N, fv, cudaMemcpyDeviceToDevice);
+        lambda[2 * i] = right.theta[cand[i]].real();
+        lambda[2 * i + 1] = right.theta[cand[i]].imag();
+    }
+    if (e == cudaSuccess) e = launch_to_canonical(PREC_F64, tmp, fv, Rc, N, (int)g->V, m, 0);
+    for (int i = 0; i < m && e == cudaSuccess; ++i)
+        e = cudaMemcpy(tmp + (size_t)i * N, c.Q + (size_t)lsel[i] * N, fv, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = launch_to_canonical(PREC_F64, tmp, fv, Lc, N, (int)g->V, m, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(Rblk);
+    if (e != cudaSuccess) {
+        cudaFree(Rc); cudaFree(Lc); cudaFree(tmp);
+        return lib_fail(OVS_ECUDA, "deflate_setup: gathering eigenvectors failed");
+    }
+    rc = install_deflation(g, m, Rc, Lc, lambda.data());
+    cudaFree(Rc);
+    cudaFree(Lc);
+    cudaFree(tmp);
+    if (rc < 0) return rc;
+    if (eig_out)
+        for (int i = 0; i < 2 * m; ++i) eig_out[i] = lambda[i];
+    double rmax = 0.0;
+    for (int i = 0; i < m; ++i) rmax = std::max(rmax, right.resid[cand[i]]);
+    g->setup_resid = rmax;
+    g->setup_iters[0] = right.iters;
+    g->setup_iters[1] = left.iters;
+    g->setup_matvecs = right.matvecs + left.matvecs;
+    if (!ok) {
+        snprintf(msg, sizeof(msg),
+                 "deflate_setup: pairs did not all reach tol (right %s after %d iterations, left %s after %d, "
+                 "worst left/right eigenvalue mismatch %.2e); basis installed",
+                 right.converged ? "converged" : "not converged", right.iters,
+                 left.converged ? "converged" : "not converged", left.iters, worst_match);
+        return lib_fail(OVS_EEIG, msg);
+    }
+    return OVS_OK;
 }
+
 }  // namespace ovs

@@ -1,0 +1,87 @@
+// Private definition of the library handle (shared by api.cu and eig.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/ovsign.h"
+#include "common.cuh"
+
+struct VecWork {  // per-right-hand-side vectors
+    int nrhs = 0, prec = -1;
+    void* xint = nullptr;  // [nrhs][N] precision prec (x, then x_ominus)
+    void* wvec = nullptr;  // [nrhs][N] precision prec (Arnoldi w)
+    void* yacc = nullptr;  // [nrhs][N] complex128 internal (y accumulator)
+    void* sx = nullptr;    // [nrhs][N] complex128 canonical staging (host x)
+    void* sy = nullptr;    // [nrhs][N] complex128 canonical staging (host y)
+};
+
+struct KryWork {  // Krylov basis and small matrices
+    int nrhs = 0, kmax = 0, prec = -1, jcap = 0, nblk = 0;
+    void* basis = nullptr;       // [nrhs][kmax+1][N] precision prec
+    void* H = nullptr;           // [nrhs][(kmax+1) x kmax] complex128, column-major
+    void* htmp = nullptr;        // [nrhs][jcap] complex128: reduced inner products of a sweep
+    void* dcoef = nullptr;       // [nrhs] complex128
+    void* partial = nullptr;     // [nrhs][nblk][jcap] complex128
+    double* norm_part = nullptr; // [nrhs][nblk]
+    double* beta = nullptr;
+    double* inv_beta = nullptr;
+    double* hnorm2 = nullptr;
+    int* active = nullptr;
+    int* k_used = nullptr;
+    int* iters = nullptr;
+    int* status = nullptr;
+    void* coeff = nullptr;  // [nrhs][kmax] complex128
+    void* newton = nullptr; // [nrhs][2 kmax^2] complex128
+    void* cdef = nullptr;   // [nrhs][m] complex128 deflation coefficients
+    void* cdef2 = nullptr;  // [nrhs][m] complex128 sgn-scaled
+};
+
+struct ovs_gauge_s {
+    int dims[4];
+    ovs::Geom geom;
+    long long V = 0, N = 0;
+    int prec = OVS_F64;
+    int device = 0, num_sms = 148;
+    bool mu_set = false;
+    double mu = 0.0, m_w = 0.0, kappa = 0.0;
+    void* links64 = nullptr;  // [4][9][V] double2
+    void* links32 = nullptr;  // [4][9][V] float2 (OVS_MIXED)
+    // deflation basis (internal layout)
+    int m = 0;
+    void* R64 = nullptr;  // [m][N] double2 planes
+    void* L64 = nullptr;  // biorthonormalised
+    void* R32 = nullptr;  // [m][N/2] float4 planes
+    void* L32 = nullptr;
+    double* sgn = nullptr;  // device [m]
+    std::vector<double> lambda;  // host 2m
+    VecWork vw;
+    KryWork kw;
+    int last_nrhs = 0;
+    cudaStream_t last_stream = nullptr;
+    // tracing (ovs_profile_*)
+    struct Pending {
+        int cls, ev;
+    };
+    bool timing = false;
+    double prof_ms[OVS_PROF_NCLASS] = {};
+    double prof_bytes[OVS_PROF_NCLASS] = {};
+    long long prof_launches[OVS_PROF_NCLASS] = {};
+    std::vector<cudaEvent_t> events;
+    std::vector<Pending> pending;
+    cudaStream_t prof_stream = nullptr;
+    // statistics of the last ovs_deflate_setup
+    int setup_iters[2] = {0, 0};
+    long long setup_matvecs = 0;
+    double setup_resid = 0.0;
+    double setup_budget_s = 0.0;
+};
+
+
+namespace ovs {
+int lib_fail(int code, const char* msg);
+// Install R (right) and L (left) vectors given as device canonical
+// complex128 [m][N]; L is biorthonormalised against R.
+int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, const double* lambda);
+}  // namespace ovs

@@ -15,6 +15,15 @@ enum { PREC_F64 = 0, PREC_F32 = 1 };
 cudaError_t launch_wilson(int prec, bool gamma5, const void* links, const void* in, size_t in_stride, void* out,
                           size_t out_stride, const Geom& g, int nrhs, double kappa, double mu, const int* active,
                           cudaStream_t st);
+// out = ah * H_w in + bx * X + by * Y (fused Chebyshev-recurrence step)
+cudaError_t launch_wilson_axpy(int prec, const void* links, const void* in, size_t in_stride, void* out,
+                               size_t out_stride, const void* X, size_t xs, double bx, const void* Y, size_t ys,
+                               double by, double ah, const Geom& g, int nrhs, double kappa, double mu,
+                               cudaStream_t st);
+// flat complex128 <-> complex64 conversion of internal fields (to_prec = target)
+cudaError_t launch_convert(int to_prec, const void* in, void* out, long long ncplx, cudaStream_t st);
+// uniform (-1,1) complex entries from a hash of (seed, index)
+cudaError_t launch_random_fill(void* q, long long ncplx, uint64_t seed, cudaStream_t st);
 cudaError_t launch_to_internal(int prec, const void* canon, size_t canon_stride_cplx, void* out, size_t out_stride,
                                int V, int nrhs, cudaStream_t st);
 cudaError_t launch_to_canonical(int prec, const void* in, size_t in_stride, void* canon, size_t canon_stride_cplx,
@@ -31,12 +40,16 @@ struct BlasPlan {
 };
 BlasPlan blas_plan(long long nunits, int nrhs, int num_sms);
 
-// partial[r][b][i] = sum over block b of conj(V_r,i) . w_r, i < J
-// (basis of rhs r at basis + r*basis_rhs_stride units, vector i at
-// + i*vec_stride units).
-cudaError_t launch_dots(int prec, const void* basis, long long basis_rhs_stride, long long vec_stride, int J,
-                        const void* w, long long w_rhs_stride, long long nunits, const BlasPlan& plan, int nrhs,
-                        void* partial, const int* active, cudaStream_t st);
+// Inner products of one sweep over J basis vectors (K2 / K5):
+// partial[r][b][S], S = gdots_stride(nw, J) = nw*J + 2, holds for row
+// block b: s_i = V_i^H u (i < J), then (nw == 2) t_i = V_i^H z, then
+// (u^H u, 0) and u^H z if extras. Basis of rhs r at basis + r*basis_rhs_stride
+// units (0: shared by all rhs), vector i at + i*vec_stride units.
+int gdots_stride(int nw, int J);
+cudaError_t launch_gdots(int prec, int nw, const void* basis, long long basis_rhs_stride, long long vec_stride,
+                         int J, const void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
+                         bool extras, long long nunits, const BlasPlan& plan, int nrhs, void* partial,
+                         const int* active, cudaStream_t st);
 
 // out_r = in_r + alpha * sum_{i<J_r} V_r,i c_r,i   (coef: complex128 [r][coef_stride])
 // J_r = J (host) or Jdev[r] (device, if Jdev != nullptr, clamped to J).
@@ -49,24 +62,23 @@ cudaError_t launch_update(int prec_v, int prec_out, const void* basis, long long
                           long long nunits_v, const BlasPlan& plan, int nrhs, double* norm_partial,
                           const int* active, cudaStream_t st);
 
-// sum partial[r][b][i] over b -> out[r*out_stride + i] (= or +=)
-cudaError_t launch_reduce(const void* partial, int nblk, int J, int nrhs, void* out, long long out_stride,
-                          bool accumulate, const int* active, cudaStream_t st);
+// sum partial[r][b][i] (row stride pstride) over b -> out[r*out_stride + i], i < J
+cudaError_t launch_reduce(const void* partial, int nblk, int pstride, int J, int nrhs, void* out,
+                          long long out_stride, bool accumulate, const int* active, cudaStream_t st);
 
-// After the second Gram-Schmidt update of Arnoldi step j (0-based): beta =
-// sqrt(sum norm_partial), H[j+1][j] = beta (H column-major, leading dim ldh),
-// breakdown test, inv_beta, k_used, active.
-cudaError_t launch_finalize(const double* norm_partial, int nblk, int nrhs, void* H, long long h_rhs_stride,
-                            int ldh, int j, double* hnorm2, double* inv_beta, int* active, int* k_used,
-                            cudaStream_t st);
-
-// Start of Arnoldi: beta0 = sqrt(sum norm_partial); inv_beta; active = beta0 > 0.
-cudaError_t launch_init_beta(const double* norm_partial, int nblk, int nrhs, double* beta, double* inv_beta,
-                             double* hnorm2, int* active, int* k_used, cudaStream_t st);
-
-// out_r = in_r * inv_beta[r] (units of precision prec)
-cudaError_t launch_scale(int prec, const void* in, long long in_rhs_stride, void* out, long long out_rhs_stride,
-                         long long nunits, const double* inv_beta, int nrhs, const int* active, cudaStream_t st);
+// Arnoldi step j of CGS2 with delayed reorthogonalisation (see blas.cu).
+cudaError_t launch_arnoldi_step(const void* red, long long red_stride, int j, void* H, long long h_rhs, int ldh,
+                                double* beta0, double* inv_beta, void* dcoef, double* hnorm2, int* active,
+                                int* k_used, int nrhs, cudaStream_t st);
+// v_j = (u - V s)/beta -> slot J; u <- (z - V t)/beta - v_j d
+cudaError_t launch_arnoldi_update(int prec, void* basis, long long basis_rhs_stride, long long vec_stride, int J,
+                                  const void* red, long long red_stride, const double* inv_beta, const void* dcoef,
+                                  void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
+                                  long long nunits, const BlasPlan& plan, int nrhs, const int* active,
+                                  cudaStream_t st);
+// last column: H[:k][k-1] += s, H[k][k-1] = ||u - V s||
+cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, void* H, long long h_rhs, int ldh,
+                                 const int* active, int nrhs, cudaStream_t st);
 
 // c'_r,i = sgn(Re lambda_i) * c_r,i
 cudaError_t launch_sign_scale(const void* c, const double* sgn, int m, int nrhs, void* out, cudaStream_t st);

@@ -1,0 +1,128 @@
+"""GPU deflation set-up (ovs_deflate_setup) against the CPU oracle.
+
+The installed basis must hold eigenpairs of the oracle's H_w(mu): right
+residuals ||H r - lambda r|| and left residuals ||H^H l - conj(lambda) l||
+within the requested tolerance (relative to ||H||), L^H R = I, and the
+eigenvalues equal to the oracle's critical set (smallest |Re lambda|).
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import deflation, freefield, lattice, signfun
+
+pytestmark = pytest.mark.gpu
+
+MW = -1.5
+
+
+def _check_basis(gpu, g, h, tol):
+    R, L, lam = gpu.deflate_get(g)
+    hnorm = spla.svds(h, k=1, return_singular_vectors=False)[0]
+    for i in range(len(lam)):
+        r = R[i] / np.linalg.norm(R[i])
+        assert np.linalg.norm(h @ r - lam[i] * r) <= 10 * tol * hnorm
+        li = L[i] / np.linalg.norm(L[i])
+        assert np.linalg.norm(h.conj().T @ li - np.conj(lam[i]) * li) <= 10 * tol * hnorm
+    gram = L.conj() @ R.T
+    assert np.abs(gram - np.eye(len(lam))).max() < 1e-9
+    return R, L, lam
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_setup_matches_dense_oracle(gpu, prec):
+    dims, mu, m, tol = (2, 4, 4, 4), 0.2, 12, 1e-10
+    links = synth.gauge_links(dims, 4, 0.7)
+    h = lattice.hw_operator(links, dims, mu, MW)
+    g = gpu.create_gauge_from_links(dims, links, prec)
+    gpu.set_mu(g, mu, MW)
+    lam_gpu, st = gpu.deflate_setup(g, m, tol)
+    assert st == 0
+    _check_basis(gpu, g, h, tol)
+    lam_ref, _, _ = deflation.critical_pairs_dense(h.toarray(), m)
+    assert np.allclose(np.sort(np.abs(lam_gpu.real)), np.sort(np.abs(lam_ref.real)), rtol=1e-8, atol=1e-10)
+    assert np.allclose(np.sort(np.abs(lam_gpu)), np.sort(np.abs(lam_ref)), rtol=1e-8, atol=1e-10)
+    g.destroy()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_setup_wide_spectrum_mu03(gpu, prec):
+    """mu = 0.3 widens the bow-tie (|Im lambda| up to 4 kappa sinh mu): the
+    ellipse filter must still converge; 4^3 x 8, eps 0.5, m = 20, against
+    the oracle's ARPACK shift-invert critical set."""
+    dims, mu, m, tol = (4, 4, 4, 8), 0.3, 20, 1e-10
+    links = synth.gauge_links(dims, 1, 0.5)
+    h = lattice.hw_operator(links, dims, mu, MW)
+    g = gpu.create_gauge_from_links(dims, links, prec)
+    gpu.set_mu(g, mu, MW)
+    lam_gpu, st = gpu.deflate_setup(g, m, tol)
+    assert st == 0
+    _check_basis(gpu, g, h, tol)
+    hm = lattice.hw_operator(links, dims, -mu, MW)
+    lam_ref, _, _ = deflation.critical_pairs_sparse(h, hm, m)
+    assert np.allclose(np.sort(np.abs(lam_gpu.real)), np.sort(np.abs(lam_ref.real)), rtol=1e-8)
+    stats = gpu.deflate_stats(g)
+    assert stats["iterations"][0] >= 1 and stats["matvecs"] > 0 and stats["max_resid"] <= tol
+    g.destroy()
+
+
+def test_setup_matches_sparse_oracle_6to4(gpu):
+    """6^4, eps 0.7, mu 0.2, m 30: eigenvalues equal the oracle's critical set
+    (ARPACK shift-invert on H(mu) and H(-mu), smallest |Re lambda| kept)."""
+    dims, mu, m, tol = (6, 6, 6, 6), 0.2, 30, 1e-9
+    links = synth.gauge_links(dims, 3, 0.7)
+    h = lattice.hw_operator(links, dims, mu, MW)
+    g = gpu.create_gauge_from_links(dims, links, gpu.MIXED)
+    gpu.set_mu(g, mu, MW)
+    lam_gpu, st = gpu.deflate_setup(g, m, tol)
+    assert st == 0
+    _check_basis(gpu, g, h, tol)
+    hm = lattice.hw_operator(links, dims, -mu, MW)
+    lam_ref, _, _ = deflation.critical_pairs_sparse(h, hm, m)
+    assert np.allclose(np.sort(np.abs(lam_gpu.real)), np.sort(np.abs(lam_ref.real)), rtol=1e-7)
+    g.destroy()
+
+
+def test_setup_budget_gives_eeig_with_basis(gpu):
+    """A zero-iteration budget: the set-up stops early, installs the current
+    Ritz pairs and reports OVS_EEIG (not a crash, not a hang)."""
+    dims, mu, m = (4, 4, 4, 4), 0.2, 16
+    g = gpu.create_gauge(dims, 3, 0.7, gpu.MIXED)
+    gpu.set_mu(g, mu, MW)
+    gpu.set_setup_budget(g, 1e-9)
+    lam, st = gpu.deflate_setup(g, m, 1e-12, allow_unconverged=True)
+    assert st == -5 and len(lam) == m
+    R, L, lam2 = gpu.deflate_get(g)
+    assert R.shape == (m, 3072)
+    g.destroy()
+
+
+def test_setup_deflation_accelerates_sign(gpu):
+    """With the GPU basis, LR-deflated sign applications converge faster
+    (Sec. 6): at fixed k the error against the dense sgn falls with m."""
+    dims, mu = (2, 4, 4, 4), 0.2
+    links = synth.gauge_links(dims, 4, 0.7)
+    h = lattice.hw_operator(links, dims, mu, MW)
+    hd = h.toarray()
+    x = synth.gaussian_vectors(1536, 1, 3)
+    exact = signfun.sgn_apply_dense(hd, x[0])
+    import torch
+    g = gpu.create_gauge_from_links(dims, links, gpu.F64)
+    gpu.set_mu(g, mu, MW)
+    yd = torch.empty((1, 1536), dtype=torch.complex128, device="cuda:0")
+    errs = []
+    for m in (0, 8, 24):
+        if m:
+            gpu.deflate_setup(g, m, 1e-11)
+        else:
+            gpu.deflate_load(g, None, None, np.zeros(0))
+        gpu.sign_apply(g, torch.from_numpy(x).cuda(), yd, 60, prec=gpu.F64)
+        errs.append(np.linalg.norm(yd.cpu().numpy()[0] - exact) / np.linalg.norm(exact))
+    assert errs[0] > errs[1] > errs[2]
+    # and parity with the oracle run on the same basis
+    R, L, lam = gpu.deflate_get(g)
+    ref, _ = deflation.lr_sign_apply(lambda q: h @ q, x[0], R.T, L.T, lam, 60)
+    assert np.linalg.norm(yd.cpu().numpy()[0] - ref) / np.linalg.norm(ref) < 1e-12
+    g.destroy()
