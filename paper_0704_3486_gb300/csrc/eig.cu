@@ -398,9 +398,13 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
                       std::max(1.0, (double)fp.deg / std::max(1, last_deg));
         last_deg = fp.deg;
         // precision: complex64 until its rounding limits progress
-        // complex64 filtering until its rounding limits progress: switch when
-        // the residuals approach FP32 precision (or stall close to it)
-        if (fprec == PREC_F32 && (rmax < 3e-6 || (rmax < 1e-4 && rmax > 0.5 * last_rmax))) fprec = PREC_F64;
+        // complex64 filtering until it stops making progress (FP32 rounding,
+        // or noise amplified by the filter): then complex128, whose stencil
+        // is FP64-ALU bound and costs ~20x more per degree
+        if (fprec == PREC_F32 && (rmax < 3e-6 || rmax > 0.5 * last_rmax)) {
+            fprec = PREC_F64;
+            last_iter_s *= 20.0;
+        }
         last_rmax = rmax;
     }
     // hand the Ritz vectors (now in Q) to the caller, sorted by |theta|
