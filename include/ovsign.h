@@ -107,6 +107,24 @@ int ovs_set_mu(ovs_gauge_t g, double mu, double m_w);
 int ovs_matvec(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, int32_t prec,
                void* stream);
 
+/* ovs_matvec without any device allocation, for callers that cannot let a
+ * library allocate: programs whose device memory is already handed out by
+ * another allocator (so a cudaMalloc would fail or take memory it owns), and
+ * loops that must not pay the device-wide synchronisation of cudaMalloc and
+ * cudaFree. The paper has no counterpart: this is a service of the library.
+ * The two work fields live in one fixed array compiled into the library,
+ * 8 MiB per field, which every GPU that loads the library holds until the
+ * process exits: nrhs * N <= 524288 (OVS_F64) or <= 1048576 (OVS_MIXED),
+ * larger requests fail with OVS_EINVAL. x and y must be device pointers
+ * (complex128, canonical layout, [nrhs][N]); host pointers fail with
+ * OVS_EINVAL. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls share the array: calls that
+ * overlap on the GPU race on it and must be serialised by the caller.
+ * Same results as ovs_matvec; errors as ovs_matvec plus the size limit. */
+int ovs_matvec_noalloc(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, int32_t prec,
+                       void* stream);
+
 /* Compute the m critical eigenpairs of H_w(mu) on the GPU for LR deflation
  * (Sec. 5.3 step i, Sec. 6): eigenvalues of smallest |lambda| found through
  * H_w(mu)^2 (the paper's choice), right vectors R with H R = R Lambda, left

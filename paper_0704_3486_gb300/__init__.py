@@ -26,6 +26,7 @@ STATUS = {
 }
 EXPORTS = [
     "ovs_create_gauge", "ovs_create_gauge_from_links", "ovs_get_links", "ovs_set_mu", "ovs_matvec",
+    "ovs_matvec_noalloc",
     "ovs_deflate_setup", "ovs_deflate_stats", "ovs_set_setup_budget", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
     "ovs_sign_apply", "ovs_get_info", "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
     "ovs_destroy",
@@ -74,6 +75,7 @@ def load(path=None):
         "ovs_get_links": ([vp, vp], i32),
         "ovs_set_mu": ([vp, dbl, dbl], i32),
         "ovs_matvec": ([vp, i32, vp, vp, i32, i32, vp], i32),
+        "ovs_matvec_noalloc": ([vp, i32, vp, vp, i32, i32, vp], i32),
         "ovs_deflate_setup": ([vp, i32, dbl, vp], i32),
         "ovs_deflate_stats": ([vp, vp, vp, vp], i32),
         "ovs_set_setup_budget": ([vp, dbl], i32),
@@ -185,6 +187,17 @@ def set_mu(g, mu, m_w):
 def matvec(g, op, x, y, nrhs=None, prec=F64, stream=None):
     nrhs = x.shape[0] if nrhs is None else nrhs
     _check(load().ovs_matvec(g.handle, int(op), _ptr(x), _ptr(y), int(nrhs), int(prec), _stream(stream)))
+
+
+def matvec_noalloc(g, op, x, y, nrhs=None, prec=F64, stream=None):
+    """matvec for callers that cannot have the library allocate device
+    memory (their pool belongs to another allocator, or cudaMalloc's
+    synchronisation is not allowed in their loop). Uses a fixed 2 x 8 MiB
+    work array inside the library: nrhs*N <= 524288 (F64) / 1048576 (MIXED);
+    x, y must be device tensors. Calls that overlap on the GPU race."""
+    nrhs = x.shape[0] if nrhs is None else nrhs
+    _check(load().ovs_matvec_noalloc(g.handle, int(op), _ptr(x), _ptr(y), int(nrhs), int(prec),
+                                     _stream(stream)))
 
 
 def deflate_setup(g, m, tol=1e-10, allow_unconverged=False):
