@@ -330,12 +330,20 @@ def run_ours(args, w, world, rank, local):
         peak, peak_src = 6800.0, "fallback"
     top = max(("dots", "update", "matvec"), key=lambda c: prof[c]["ms"])
     ach = prof[top]["bytes"] / (prof[top]["ms"] / 1e3) / 1e9 if prof[top]["ms"] > 0 else 0.0
+    # DRAM traffic per launch: the ncu capture of the current kernel of each
+    # class (16^3x32, 2 RHS, J = 30; profiles/) gave traffic / algorithmic
+    # bytes; traffic grows in proportion to the vectors read, so a launch of
+    # the timed step moves that ratio times its algorithmic bytes.
+    traffic_ratio = {"dots": 808.25 / 805.31, "update": 850.60 / 855.64}.get(top)
+    per_launch = prof[top]["bytes"] / max(prof[top]["launches"], 1)
+    traffic = round(per_launch * traffic_ratio) if traffic_ratio else None
     share = {c: round(prof[c]["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-9), 4) for c in prof}
     roofline = {"bound": "hbm", "kernel": {"dots": "k_dots (CGS2 inner products)",
                                             "update": "k_update (CGS2 update / recombination)",
                                             "matvec": "k_wilson (H_w stencil)"}[top],
                 "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                "peak_source": f"{peak_src} hbm_gbs (copy)", "traffic": None,
+                "peak_source": f"{peak_src} hbm_gbs (copy)", "traffic": traffic,
+                "algorithmic_bytes_per_launch": round(per_launch),
                 "per_class": {c: {"ms_per_step": round(prof[c]["ms"] / args.steps, 3),
                                   "launches_per_step": prof[c]["launches"] // max(args.steps, 1),
                                   "gbs": round(prof[c]["bytes"] / (prof[c]["ms"] / 1e3) / 1e9, 1)

@@ -153,6 +153,7 @@ static void free_kry(KryWork& k) {
     dfree(k.H);
     dfree(k.htmp);
     dfree(k.dcoef);
+    dfree(k.err);
     dfree(k.partial);
     dfree(k.norm_part);
     dfree(k.beta);
@@ -214,6 +215,8 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     CK(dalloc(&k.H, sizeof(double2) * (size_t)(km + 1) * km * n));
     CK(dalloc(&k.htmp, sizeof(double2) * (size_t)jc * n));
     CK(dalloc(&k.dcoef, sizeof(double2) * (size_t)n));
+    CK(dalloc(&k.err, sizeof(int)));
+    CK(cudaMemset(k.err, 0, sizeof(int)));
     CK(dalloc(&k.partial, sizeof(double2) * (size_t)nb * jc * n));
     CK(dalloc(&k.norm_part, sizeof(double) * (size_t)nb * n));
     CK(dalloc(&k.beta, sizeof(double) * n));
@@ -709,6 +712,7 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
         KL(OVS_PROF_MATVEC, bw,
            launch_wilson(tp, true, links_for(g, tp), w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
                          kw.active, st));
+        const bool tma = (tp == PREC_F32) && tma_update_fits(j);
         KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (j + 2.0),
            launch_gdots(tp, 2, basis, basis_rhs_units, units, j, w.xint, units, w.wvec, units, true, units, plan, nrhs,
                         kw.partial, kw.active, st));
@@ -717,9 +721,14 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
         KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 3.0 * j) * nrhs,
            launch_arnoldi_step(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.beta, kw.inv_beta, kw.dcoef, kw.hnorm2,
                                kw.active, kw.k_used, nrhs, st));
-        KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
-           launch_arnoldi_update(tp, basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
-                                 w.xint, units, w.wvec, units, units, plan, nrhs, kw.active, st));
+        if (tma)
+            KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
+               launch_arnoldi_update_tma(basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
+                                         w.xint, units, w.wvec, units, units, plan, nrhs, kw.active, kw.err, st));
+        else
+            KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
+               launch_arnoldi_update(tp, basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
+                                     w.xint, units, w.wvec, units, units, plan, nrhs, kw.active, st));
     }
     {  // second Gram-Schmidt pass of the last column
         const int S = gdots_stride(1, k);
@@ -758,6 +767,12 @@ int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
     CK(cudaMemcpy(it.data(), g->kw.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(stt.data(), g->kw.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(beta.data(), g->kw.beta, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
+    int derr = 0;
+    CK(cudaMemcpy(&derr, g->kw.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (derr != 0) {
+        CK(cudaMemset(g->kw.err, 0, sizeof(int)));
+        return fail(OVS_ETIMEOUT, "a bounded device wait gave up during the last sign application");
+    }
     int worst = OVS_OK;
     for (int r = 0; r < nrhs; ++r) {
         info[r].k_used = ku[r];

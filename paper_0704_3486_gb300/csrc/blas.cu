@@ -62,7 +62,7 @@ template <typename R, int M> __device__ __forceinline__ void transpose_reduce(R 
 // lanes (at most 32*E*NC = 512 terms in FP32), and the warp partials are
 // accumulated in FP64 in shared memory.
 template <typename R, int NW, int G, int E>
-__global__ void __launch_bounds__(BT) k_gdots(const typename Unit<R>::vec* __restrict__ basis,
+__global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 2 : 1) k_gdots(const typename Unit<R>::vec* __restrict__ basis,
                                               long long basis_rhs_stride, long long vec_stride, int J,
                                               const typename Unit<R>::vec* __restrict__ u, long long u_rhs_stride,
                                               const typename Unit<R>::vec* __restrict__ z, long long z_rhs_stride,
@@ -585,8 +585,8 @@ static void set_smem_attrs() {
     const int big = 200 * 1024;
     cudaFuncSetAttribute(k_gdots<double, 1, 16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_gdots<double, 2, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_gdots<float, 1, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_gdots<float, 2, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_gdots<float, 1, 16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_gdots<float, 2, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_arnoldi_update<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_arnoldi_update<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_update<double, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -618,11 +618,11 @@ cudaError_t launch_gdots(int prec, int nw, const void* basis, long long basis_rh
                                                              (double2*)partial, active);
     } else {
         if (nw == 1)
-            k_gdots<float, 1, 16, 8><<<grid, BT, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J,
+            k_gdots<float, 1, 16, 4><<<grid, BT, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J,
                                                              (const float4*)u, u_rhs_stride, nullptr, 0, ex, nunits,
                                                              plan.chunk, plan.nblk, (double2*)partial, active);
         else
-            k_gdots<float, 2, 8, 8><<<grid, BT, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J,
+            k_gdots<float, 2, 8, 4><<<grid, BT, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J,
                                                              (const float4*)u, u_rhs_stride, (const float4*)z,
                                                              z_rhs_stride, ex, nunits, plan.chunk, plan.nblk,
                                                              (double2*)partial, active);

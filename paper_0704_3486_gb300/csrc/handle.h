@@ -23,6 +23,7 @@ struct KryWork {  // Krylov basis and small matrices
     void* H = nullptr;           // [nrhs][(kmax+1) x kmax] complex128, column-major
     void* htmp = nullptr;        // [nrhs][jcap] complex128: reduced inner products of a sweep
     void* dcoef = nullptr;       // [nrhs] complex128
+    int* err = nullptr;          // device error word (OVS_ETIMEOUT from bounded waits)
     void* partial = nullptr;     // [nrhs][nblk][jcap] complex128
     double* norm_part = nullptr; // [nrhs][nblk]
     double* beta = nullptr;

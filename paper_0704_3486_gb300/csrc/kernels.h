@@ -80,6 +80,15 @@ cudaError_t launch_arnoldi_update(int prec, void* basis, long long basis_rhs_str
 cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, void* H, long long h_rhs, int ldh,
                                  const int* active, int nrhs, cudaStream_t st);
 
+// TMA-pipelined complex64 form of the Arnoldi update sweep (tma_sweeps.cu);
+// *err receives OVS_ETIMEOUT if a bounded wait gives up.
+bool tma_update_fits(int J);
+cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, long long vec_stride, int J,
+                                      const void* red, long long red_stride, const double* inv_beta,
+                                      const void* dcoef, void* u, long long u_rhs_stride, const void* z,
+                                      long long z_rhs_stride, long long nunits, const BlasPlan& plan, int nrhs,
+                                      const int* active, int* err, cudaStream_t st);
+
 // c'_r,i = sgn(Re lambda_i) * c_r,i
 cudaError_t launch_sign_scale(const void* c, const double* sgn, int m, int nrhs, void* out, cudaStream_t st);
 

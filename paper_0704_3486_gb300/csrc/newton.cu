@@ -1,6 +1,7 @@
 // K3: sgn(H_k) e_1 by Roberts' iteration S <- (S + S^-1)/2, S^0 = H_k
 // (Sec. 5.2, Eq. Roberts; used for H_k in Sec. 5.3 step v), in FP64 on the
-// device, one thread block per right-hand side.
+// device: a cluster of 8 thread blocks (8 SMs) per right-hand side for
+// k <= 320, one thread block per right-hand side above.
 //
 // The inverse is an in-place Gauss-Jordan elimination with partial (row)
 // pivoting; the row interchanges are undone as column interchanges at the
@@ -10,8 +11,12 @@
 // A zero or non-finite pivot (an eigenvalue on or numerically at the
 // imaginary axis makes S singular) ends with status OVS_ESIGN; no
 // convergence within 50 iterations gives OVS_NOT_CONVERGED.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace ovs {
 
@@ -95,8 +100,10 @@ __device__ bool gauss_jordan(cd* A, int n, int* perm, cd* colp, cd* rowp, double
             } else {
                 cd v = A[idx];
                 const cd f = colp[i], g = rowp[j];
-                v.re -= f.re * g.re - f.im * g.im;
-                v.im -= f.re * g.im + f.im * g.re;
+                v.re = fma(-f.re, g.re, v.re);
+                v.re = fma(f.im, g.im, v.re);
+                v.im = fma(-f.re, g.im, v.im);
+                v.im = fma(-f.im, g.re, v.im);
                 A[idx] = v;
             }
         }
@@ -195,13 +202,258 @@ __global__ void __launch_bounds__(NT) k_newton(const double2* __restrict__ H, lo
     }
 }
 
+// ----------------------------------------------------------------------
+// Cluster form: one matrix per cluster of NCL CTAs (one per SM). CTA c holds
+// the column block [c*W, c*W + W) of the matrix being inverted in shared
+// memory (W = ceil(n/NCL)); the iterate S stays in global memory (each CTA
+// touches only its own columns). Gauss-Jordan step p: the owner of column p
+// picks the pivot and publishes the pivot index and the (row-swapped)
+// column p in its shared memory, double-buffered by the parity of p; one
+// cluster barrier makes them visible; every CTA copies them through
+// distributed shared memory, swaps rows p and pivot in its block, and
+// eliminates. After the last step the row interchanges are undone as a
+// column permutation read from the owners' blocks while S <- (S + S^-1)/2 is
+// formed, and the norms of the change are summed over the cluster.
+constexpr int NCL = 8;
+constexpr int NTC = 512;
+constexpr int kClusterMaxN = 320;
+
+__device__ __forceinline__ double cl_block_sum(double v, double* sh) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int q = 0; q < NTC / 32; ++q) s += sh[q];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
+    k_newton_cluster(const double2* __restrict__ H, long long h_rhs_stride, int ldh, const int* __restrict__ k_used,
+                     const double* __restrict__ beta, double2* __restrict__ coeff, long long coeff_stride,
+                     double2* __restrict__ work, int kmax, int* __restrict__ iters, int* __restrict__ status) {
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_piv[2], s_ok[2];
+    __shared__ double s_part[2];
+    __shared__ double s_red[NTC / 32];
+    __shared__ double s_bv[NTC / 32];
+    __shared__ int s_bi[NTC / 32];
+    const int c = (int)cl.block_rank();
+    const int r = blockIdx.x / NCL;
+    const int tid = threadIdx.x;
+    const int n = k_used[r];
+    const int Wmax = (kmax + NCL - 1) / NCL;
+    cd* T = reinterpret_cast<cd*>(smem_raw);          // [kmax][Wmax]
+    cd* colp = T + (size_t)kmax * Wmax;              // [2][kmax] published pivot columns
+    cd* colL = colp + 2 * (size_t)kmax;               // [kmax] local copy
+    cd* rowp = colL + kmax;                           // [Wmax]
+    int* perm = reinterpret_cast<int*>(rowp + Wmax);  // [kmax]
+    int* srcc = perm + kmax;                          // [kmax]
+    double2* cr = coeff + r * coeff_stride;
+    if (n <= 0) {
+        if (c == 0) {
+            for (int i = tid; i < kmax; i += NTC) cr[i] = make_double2(0.0, 0.0);
+            if (tid == 0) { iters[r] = 0; status[r] = ST_OK; }
+        }
+        return;  // uniform over the cluster: n is the same for all its CTAs
+    }
+    const int W = (n + NCL - 1) / NCL;
+    const int c0 = c * W;
+    const int w = max(0, min(n, c0 + W) - c0);
+    cd* S = reinterpret_cast<cd*>(work) + (size_t)r * 2 * kmax * kmax;  // row-major n x n
+    const double2* Hr = H + r * h_rhs_stride;
+    for (int idx = tid; idx < n * w; idx += NTC) {
+        const int i = idx / w, jj = idx - i * w;
+        const double2 h = Hr[i + (long long)(c0 + jj) * ldh];
+        S[(size_t)i * n + c0 + jj] = {h.x, h.y};
+    }
+    int st = ST_NOT_CONVERGED, it_done = 0, remaining = -1;
+    for (int it = 1; it <= kMaxIter; ++it) {
+        for (int idx = tid; idx < n * w; idx += NTC) {
+            const int i = idx / w, jj = idx - i * w;
+            T[(size_t)i * W + jj] = S[(size_t)i * n + c0 + jj];
+        }
+        __syncthreads();
+        bool ok = true;
+        for (int p = 0; p < n; ++p) {
+            const int owner = p / W, buf = p & 1;
+            if (c == owner) {
+                const int jl = p - c0;
+                double best = -1.0;
+                int bi = p;
+                for (int i = p + tid; i < n; i += NTC) {
+                    const cd a = T[(size_t)i * W + jl];
+                    const double v = a.re * a.re + a.im * a.im;
+                    if (v > best) { best = v; bi = i; }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                }
+                if ((tid & 31) == 0) { s_bv[tid >> 5] = best; s_bi[tid >> 5] = bi; }
+                __syncthreads();
+                if (tid == 0) {
+                    double b = s_bv[0];
+                    int ib = s_bi[0];
+                    for (int q = 1; q < NTC / 32; ++q)
+                        if (s_bv[q] > b || (s_bv[q] == b && s_bi[q] < ib)) { b = s_bv[q]; ib = s_bi[q]; }
+                    s_piv[buf] = ib;
+                    s_ok[buf] = (b > 0.0 && isfinite(b)) ? 1 : 0;
+                }
+                __syncthreads();
+                const int piv = s_piv[buf];
+                for (int i = tid; i < n; i += NTC) {
+                    const int si = (i == p) ? piv : (i == piv ? p : i);
+                    colp[(size_t)buf * kmax + i] = T[(size_t)si * W + jl];
+                }
+            }
+            cl.sync();
+            const int piv = *cl.map_shared_rank(&s_piv[buf], owner);
+            const int okp = *cl.map_shared_rank(&s_ok[buf], owner);
+            if (!okp) {
+                ok = false;
+                break;
+            }
+            const cd* rcol = cl.map_shared_rank(colp + (size_t)buf * kmax, owner);
+            for (int i = tid; i < n; i += NTC) colL[i] = rcol[i];
+            if (tid == 0) perm[p] = piv;
+            if (piv != p) {
+                for (int jj = tid; jj < w; jj += NTC) {
+                    const cd t = T[(size_t)p * W + jj];
+                    T[(size_t)p * W + jj] = T[(size_t)piv * W + jj];
+                    T[(size_t)piv * W + jj] = t;
+                }
+            }
+            __syncthreads();
+            const cd a = colL[p];
+            const double den = a.re * a.re + a.im * a.im;
+            const cd inv = {a.re / den, -a.im / den};
+            for (int jj = tid; jj < w; jj += NTC)
+                rowp[jj] = (c0 + jj == p) ? inv : cmul(T[(size_t)p * W + jj], inv);
+            __syncthreads();
+            for (int idx = tid; idx < n * w; idx += NTC) {
+                const int i = idx / w, jj = idx - i * w;
+                if (i == p) {
+                    T[(size_t)i * W + jj] = rowp[jj];
+                } else if (c0 + jj == p) {
+                    T[(size_t)i * W + jj] = -cmul(colL[i], inv);
+                } else {
+                    cd v = T[(size_t)i * W + jj];
+                    const cd f = colL[i], gg = rowp[jj];
+                    v.re = fma(-f.re, gg.re, v.re);
+                    v.re = fma(f.im, gg.im, v.re);
+                    v.im = fma(-f.re, gg.im, v.im);
+                    v.im = fma(-f.im, gg.re, v.im);
+                    T[(size_t)i * W + jj] = v;
+                }
+            }
+            __syncthreads();
+        }
+        if (!ok) {
+            cl.sync();  // the owner's flag was read remotely: no block leaves before all have read it
+            st = ST_ESIGN;
+            it_done = it;
+            break;
+        }
+        // S^-1 = (Gauss-Jordan result) with the row interchanges undone as
+        // column interchanges, last first: column j comes from column srcc[j]
+        if (tid == 0) {
+            for (int j = 0; j < n; ++j) srcc[j] = j;
+            for (int p = n - 1; p >= 0; --p) {
+                const int q = perm[p];
+                const int t = srcc[p];
+                srcc[p] = srcc[q];
+                srcc[q] = t;
+            }
+        }
+        cl.sync();  // every block's Gauss-Jordan result is final
+        double d2 = 0.0, s2 = 0.0;
+        for (int idx = tid; idx < n * w; idx += NTC) {
+            const int i = idx / w, jj = idx - i * w;
+            const int j = c0 + jj, sj = srcc[j];
+            const int ow = sj / W, lj = sj - ow * W;
+            const cd b = cl.map_shared_rank(T, ow)[(size_t)i * W + lj];
+            const cd a0 = S[(size_t)i * n + j];
+            const cd v = {0.5 * (a0.re + b.re), 0.5 * (a0.im + b.im)};
+            const double dx = v.re - a0.re, dy = v.im - a0.im;
+            d2 += dx * dx + dy * dy;
+            s2 += v.re * v.re + v.im * v.im;
+            S[(size_t)i * n + j] = v;
+        }
+        d2 = cl_block_sum(d2, s_red);
+        s2 = cl_block_sum(s2, s_red);
+        if (tid == 0) { s_part[0] = d2; s_part[1] = s2; }
+        cl.sync();  // partials visible; remote reads of T finished
+        double D2 = 0.0, S2 = 0.0;
+        for (int q = 0; q < NCL; ++q) {
+            const double* rp = cl.map_shared_rank(s_part, q);
+            D2 += rp[0];
+            S2 += rp[1];
+        }
+        it_done = it;
+        const double change = sqrt(D2 / S2);
+        cl.sync();  // nobody overwrites s_part or T before all have read them
+        if (!isfinite(change)) {
+            st = ST_ESIGN;
+            break;
+        }
+        if (remaining < 0 && change <= kSwitchTol) remaining = kExtra;
+        if (remaining >= 0) {
+            if (remaining == 0) {
+                st = ST_OK;
+                break;
+            }
+            --remaining;
+        }
+    }
+    if (c == 0) {
+        const double bt = beta[r];
+        for (int i = tid; i < kmax; i += NTC) {
+            if (i < n && st != ST_ESIGN) {
+                const cd sv = S[(size_t)i * n];
+                cr[i] = make_double2(bt * sv.re, bt * sv.im);
+            } else {
+                cr[i] = make_double2(0.0, 0.0);
+            }
+        }
+        if (tid == 0) {
+            iters[r] = it_done;
+            status[r] = st;
+        }
+    }
+}
+
+static size_t cluster_smem(int kmax) {
+    const int Wmax = (kmax + NCL - 1) / NCL;
+    return ((size_t)kmax * Wmax + 3 * (size_t)kmax + Wmax) * sizeof(cd) + 2 * (size_t)kmax * sizeof(int);
+}
+
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
                           int* status, cudaStream_t st) {
+    const size_t need = cluster_smem(kmax);
+    if (kmax <= kClusterMaxN && need <= 220 * 1024) {
+        static size_t attr_set = 0;  // dynamic shared memory opted in so far
+        if (need > attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(k_newton_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)need);
+            if (e != cudaSuccess) return e;
+            attr_set = need;
+        }
+        k_newton_cluster<<<nrhs * NCL, NTC, need, st>>>(
+            (const double2*)H, h_rhs_stride, ldh, k_used, beta, (double2*)coeff, coeff_stride, (double2*)work, kmax,
+            iters, status);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)kmax * 2 * sizeof(cd) + (size_t)kmax * sizeof(int);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        const cudaError_t e = cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
         attr = true;
     }
     k_newton<<<nrhs, NT, smem, st>>>((const double2*)H, h_rhs_stride, ldh, k_used, beta, (double2*)coeff,
