@@ -172,9 +172,11 @@ int ovs_deflate_restore(ovs_gauge_t g, const char* path);
 typedef struct {
     int32_t k_max;       /* Krylov dimension (Sec. 4 suggests even values) */
     int32_t check_every; /* 0: run exactly k_max steps (stop only at breakdown);
-                            >0 (even): every check_every steps estimate the
-                            error from successive coefficient vectors and
-                            stop a right-hand side once it is below tol */
+                            >0 (even): every check_every steps compute
+                            c_j = beta sgn(H_j) e_1 and stop a right-hand
+                            side once ||c_j - c_{j-check_every}|| / ||c_j||
+                            (zero-padded) is below tol; V is orthonormal,
+                            so this is the change of its Krylov part */
     int32_t prec;        /* OVS_F64 or OVS_MIXED */
     int32_t reserved;    /* must be 0 */
     double tol;          /* tolerance for check_every > 0 */
@@ -203,6 +205,21 @@ typedef struct {
  * when info is given. Errors: EINVAL, ESTATE (mu not set), ENOMEM, ECUDA. */
 int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
                    ovs_apply_info* info, void* stream);
+
+/* Batched form: n instances, each a handle with its own gauge field, mu and
+ * deflation basis, and nrhs[i] right-hand sides x[i] -> y[i] (layout and
+ * host/device rules of ovs_sign_apply; the n handles must be distinct).
+ * The instances run concurrently: each on its handle's private stream,
+ * forked from `stream` and joined back into it. Each instance's whole
+ * application (A1-A7 of ovs_sign_apply, from an internal copy of x to an
+ * internal y) is recorded once as a CUDA graph per (nrhs, opts) and
+ * replayed; set_mu, deflation changes and buffer growth drop the recorded
+ * graphs. With opts->check_every > 0 every right-hand side stops at its own
+ * Krylov dimension (uneven depths). info, if not NULL, receives
+ * sum(nrhs) reports in instance order; the call then waits for `stream`.
+ * Returns the worst status as ovs_sign_apply. */
+int ovs_sign_apply_batched(int32_t n, const ovs_gauge_t* g, const void* const* x, void* const* y,
+                           const int32_t* nrhs, const ovs_apply_opts* opts, ovs_apply_info* info, void* stream);
 
 /* Reports of the last ovs_sign_apply on this handle (waits for its stream). */
 int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs);

@@ -10,7 +10,11 @@ Readings where the paper is silent:
 * orthogonalisation: classical Gram-Schmidt applied twice (CGS2) per step:
   h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2, column = h1 + h2;
 * breakdown: if H_(j+1,j) <= 1e-12 ||H_(1:j+1,1:j)||_F the Krylov space is
-  invariant, the recurrence stops and k_used = j (the result is then exact).
+  invariant, the recurrence stops and k_used = j (the result is then exact);
+* stopping by convergence (batched form; the paper fixes k instead): every
+  `every` (even) steps form c_j = beta sgn(H_j) e_1 and stop at the first j
+  with ||c_j - c_(j-every)|| / ||c_j|| < tol (c padded with zeros); as V is
+  orthonormal this is the relative change of beta V_j sgn(H_j) e_1.
 """
 
 import numpy as np
@@ -64,3 +68,25 @@ def arnoldi_sign(matvec, x, k, **newton_kw):
     coeff = beta * s[:, 0]
     y = v[:, :k_used] @ coeff
     return y, dict(k_used=k_used, beta=beta, newton_iters=it, coeff=coeff, H=h)
+
+
+def arnoldi_sign_adaptive(matvec, x, k_max, every, tol, **newton_kw):
+    """Eq. yproj3 with k chosen by the convergence estimate above.
+
+    Returns (y, info) with info = dict(k_used, est, beta, coeff).
+    """
+    v, h, beta, k_run = arnoldi(matvec, x, k_max)
+    c_prev = np.zeros(0, dtype=np.complex128)
+    est = 0.0
+    for j in range(every, k_run + 1, every):
+        s, _ = roberts_sign(h[:j, :j], **newton_kw)
+        c = beta * s[:, 0]
+        prev = np.zeros(j, dtype=np.complex128)
+        prev[: c_prev.shape[0]] = c_prev
+        est = np.linalg.norm(c - prev) / np.linalg.norm(c)
+        c_prev = c
+        if est < tol:
+            return v[:, :j] @ c, dict(k_used=j, est=est, beta=beta, coeff=c)
+    y, info = arnoldi_sign(matvec, x, k_run, **newton_kw)
+    info["est"] = est
+    return y, info

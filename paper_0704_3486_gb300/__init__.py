@@ -28,7 +28,7 @@ EXPORTS = [
     "ovs_create_gauge", "ovs_create_gauge_from_links", "ovs_get_links", "ovs_set_mu", "ovs_matvec",
     "ovs_matvec_noalloc",
     "ovs_deflate_setup", "ovs_deflate_stats", "ovs_set_setup_budget", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
-    "ovs_sign_apply", "ovs_get_info", "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
+    "ovs_sign_apply", "ovs_sign_apply_batched", "ovs_get_info", "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
     "ovs_destroy",
 ]
 PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout"]
@@ -84,6 +84,8 @@ def load(path=None):
         "ovs_deflate_save": ([vp, ctypes.c_char_p], i32),
         "ovs_deflate_restore": ([vp, ctypes.c_char_p], i32),
         "ovs_sign_apply": ([vp, vp, vp, i32, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp], i32),
+        "ovs_sign_apply_batched": ([i32, vp, vp, vp, vp, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp],
+                                   i32),
         "ovs_get_info": ([vp, ctypes.POINTER(ApplyInfo), i32], i32),
         "ovs_profile_enable": ([vp, i32], i32),
         "ovs_profile_read": ([vp, vp, vp, vp], i32),
@@ -273,6 +275,24 @@ def sign_apply(g, x, y, k_max, prec=MIXED, nrhs=None, check_every=0, tol=0.0, st
         return st, [i.as_dict() for i in info]
     return _check(lib.ovs_sign_apply(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), None,
                                      _stream(stream)))
+
+
+def sign_apply_batched(gauges, xs, ys, k_max, prec=MIXED, check_every=0, tol=0.0, stream=None, want_info=True):
+    """Batched form over several handles: y_i = sgn(H_w(mu_i)) x_i for each
+    instance i (xs[i], ys[i] of shape [nrhs_i, N_i])."""
+    n = len(gauges)
+    handles = (ctypes.c_void_p * n)(*[g.handle.value if hasattr(g.handle, "value") else g.handle for g in gauges])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x).value for x in xs])
+    yp = (ctypes.c_void_p * n)(*[_ptr(y).value for y in ys])
+    nr = (ctypes.c_int32 * n)(*[int(x.shape[0]) for x in xs])
+    opts = ApplyOpts(int(k_max), int(check_every), int(prec), 0, float(tol))
+    lib = load()
+    if want_info:
+        total = sum(int(x.shape[0]) for x in xs)
+        info = (ApplyInfo * total)()
+        st = _check(lib.ovs_sign_apply_batched(n, handles, xp, yp, nr, ctypes.byref(opts), info, _stream(stream)))
+        return st, [i.as_dict() for i in info]
+    return _check(lib.ovs_sign_apply_batched(n, handles, xp, yp, nr, ctypes.byref(opts), None, _stream(stream)))
 
 
 def get_info(g, nrhs):

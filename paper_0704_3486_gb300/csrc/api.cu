@@ -91,7 +91,7 @@ static void prof_flush(ovs_gauge_s* g) {
 
 static void prof_begin(ovs_gauge_s* g, int cls, cudaStream_t st) {
     ++g->prof_launches[cls];
-    if (!g->timing) return;
+    if (!g->timing || g->capturing) return;
     if (g->events.empty()) {
         g->events.resize(kEventPool);
         for (auto& e : g->events) cudaEventCreate(&e);
@@ -104,7 +104,7 @@ static void prof_begin(ovs_gauge_s* g, int cls, cudaStream_t st) {
 
 static void prof_end(ovs_gauge_s* g, int cls, double bytes, cudaStream_t st) {
     g->prof_bytes[cls] += bytes;
-    if (!g->timing) return;
+    if (!g->timing || g->capturing) return;
     cudaEventRecord(g->events[g->pending.back().ev + 1], st);
 }
 
@@ -154,6 +154,9 @@ static void free_kry(KryWork& k) {
     dfree(k.htmp);
     dfree(k.dcoef);
     dfree(k.err);
+    dfree(k.ccheck[0]);
+    dfree(k.ccheck[1]);
+    dfree(k.est);
     dfree(k.partial);
     dfree(k.norm_part);
     dfree(k.beta);
@@ -171,7 +174,14 @@ static void free_kry(KryWork& k) {
     k.prec = -1;
 }
 
+static void drop_graphs(ovs_gauge_s* g) {
+    for (auto& e : g->graphs) cudaGraphExecDestroy(e.exec);
+    g->graphs.clear();
+    ++g->gen;
+}
+
 static void free_deflation(ovs_gauge_s* g) {
+    drop_graphs(g);
     dfree(g->R64);
     dfree(g->L64);
     dfree(g->R32);
@@ -185,6 +195,7 @@ static int ensure_vec(ovs_gauge_s* g, int nrhs, int tprec) {
     VecWork& w = g->vw;
     if (w.nrhs >= nrhs && w.prec == tprec) return OVS_OK;
     const int n = std::max(nrhs, w.prec == tprec ? w.nrhs : 0);
+    drop_graphs(g);
     free_vec(w);
     const size_t fb = field_bytes(g->N, tprec), f64 = field_bytes(g->N, PREC_F64);
     CK(dalloc(&w.xint, fb * n));
@@ -209,6 +220,7 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     const int km = std::max(kmax, same ? k.kmax : 0);
     const int jc = std::max(gdots_stride(2, km), jneed);
     const int nb = std::max(nblk_need, blas_plan(field_units(g->N, tprec), 1, g->num_sms).nblk);
+    drop_graphs(g);
     free_kry(k);
     const size_t fb = field_bytes(g->N, tprec);
     CK(dalloc(&k.basis, fb * (size_t)(km + 1) * n));
@@ -216,6 +228,9 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     CK(dalloc(&k.htmp, sizeof(double2) * (size_t)jc * n));
     CK(dalloc(&k.dcoef, sizeof(double2) * (size_t)n));
     CK(dalloc(&k.err, sizeof(int)));
+    CK(dalloc(&k.ccheck[0], sizeof(double2) * (size_t)km * n));
+    CK(dalloc(&k.ccheck[1], sizeof(double2) * (size_t)km * n));
+    CK(dalloc(&k.est, sizeof(double) * n));
     CK(cudaMemset(k.err, 0, sizeof(int)));
     CK(dalloc(&k.partial, sizeof(double2) * (size_t)nb * jc * n));
     CK(dalloc(&k.norm_part, sizeof(double) * (size_t)nb * n));
@@ -330,7 +345,7 @@ int ovs_set_mu(ovs_gauge_t g, double mu, double m_w) {
     g->m_w = m_w;
     g->kappa = 1.0 / (8.0 + 2.0 * m_w);
     g->mu_set = true;
-    free_deflation(g);
+    free_deflation(g);  // also drops recorded applications (kappa, mu are kernel arguments)
     return OVS_OK;
 }
 
@@ -636,9 +651,11 @@ int ovs_deflate_setup(ovs_gauge_t g, int32_t m, double tol, double* eig_out) {
 }
 
 // ---------------------------------------------------------- sign apply
-int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
-                   ovs_apply_info* info, void* stream) {
-    if (!g || !x || !y || !opts) return fail(OVS_EINVAL, "NULL argument");
+}  // extern "C"
+
+// Argument checks shared by the single and batched forms.
+static int check_apply(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts) {
+    if (!g || !opts) return fail(OVS_EINVAL, "NULL argument");
     if (nrhs <= 0) return fail(OVS_EINVAL, "nrhs must be >= 1");
     if (nrhs > 65535) return fail(OVS_EINVAL, "nrhs must be <= 65535");
     if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
@@ -647,11 +664,21 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
     if ((long long)k + 1 > g->N) return fail(OVS_EINVAL, "k_max must be < N");
     if (opts->prec != OVS_F64 && opts->prec != OVS_MIXED) return fail(OVS_EINVAL, "bad prec");
     if (opts->prec == OVS_MIXED && g->prec != OVS_MIXED) return fail(OVS_ESTATE, "handle was created without OVS_MIXED");
-    if (opts->check_every != 0) return fail(OVS_EINVAL, "check_every > 0 needs the batched form");
-    cudaStream_t st = (cudaStream_t)stream;
+    const int every = opts->check_every;
+    if (every < 0 || (every % 2) != 0) return fail(OVS_EINVAL, "check_every must be 0 or a positive even number");
+    if (every > 0 && !(opts->tol > 0.0)) return fail(OVS_EINVAL, "check_every > 0 needs tol > 0");
+    return OVS_OK;
+}
+
+// Enqueue the whole application on st, from the device canonical input xd
+// to the device canonical output yd. Buffers must already be sized
+// (ensure_vec / ensure_kry); no allocation and no host synchronisation
+// happen here, so the sequence can be recorded as a CUDA graph.
+static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, const ovs_apply_opts* opts,
+                           cudaStream_t st) {
+    const int k = opts->k_max;
+    const int every = opts->check_every;
     const int tp = tprec_of(opts->prec);
-    TRY(ensure_vec(g, nrhs, tp));
-    TRY(ensure_kry(g, nrhs, k, tp));
     VecWork& w = g->vw;
     KryWork& kw = g->kw;
     const long long N = g->N;
@@ -660,7 +687,6 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
     const long long units = field_units(N, tp);
     const long long kmax = kw.kmax;
     const long long basis_rhs_units = (kmax + 1) * units;
-    const size_t basis_rhs_bytes = (size_t)(kmax + 1) * fb;
     const int ldh = (int)(kmax + 1);
     const long long h_rhs = (long long)(kmax + 1) * kmax;
     const BlasPlan plan = blas_plan(units, nrhs, g->num_sms);
@@ -668,13 +694,6 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
     char* basis = (char*)kw.basis;
 
     // input, canonical complex128 -> internal precision
-    const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
-    const void* xd = x;
-    if (!xdev) {
-        CK(cudaMemcpyAsync(w.sx, x, f64 * nrhs, cudaMemcpyHostToDevice, st));
-        xd = w.sx;
-    }
-    void* yd = ydev ? y : w.sy;
     KL(OVS_PROF_LAYOUT, bytes_layout(N, tp, nrhs), launch_to_internal(tp, xd, N, w.xint, fb, V, nrhs, st));
     CK(cudaMemsetAsync(kw.H, 0, sizeof(double2) * h_rhs * nrhs, st));
 
@@ -701,6 +720,9 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
         CK(cudaMemsetAsync(w.yacc, 0, f64 * nrhs, st));
     }
     CK(cudaMemsetAsync(kw.active, 0xff, sizeof(int) * nrhs, st));  // every rhs starts active (-1 != 0)
+    CK(cudaMemsetAsync(kw.est, 0, sizeof(double) * nrhs, st));
+    int cbuf = 0;
+    if (every > 0) CK(cudaMemsetAsync(kw.ccheck[0], 0, sizeof(double2) * kmax * nrhs, st));
 
     // Arnoldi (Sec. 4, Eq. Arnoldi; Sec. 5.3 Eq. LRArnoldi) with classical
     // Gram-Schmidt applied twice, the second pass of step j-1 done in the
@@ -721,6 +743,19 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
         KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 3.0 * j) * nrhs,
            launch_arnoldi_step(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.beta, kw.inv_beta, kw.dcoef, kw.hnorm2,
                                kw.active, kw.k_used, nrhs, st));
+        // A7 (batched form): every `every` steps, the sign of the complete
+        // H_j of each active right-hand side; stop it once successive
+        // coefficient vectors agree to tol (V orthonormal, so this is the
+        // change of its Krylov part).
+        if (every > 0 && j > 0 && j % every == 0) {
+            KL(OVS_PROF_NEWTON, 16.0 * (double)j * j * nrhs,
+               launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.ccheck[1 - cbuf], kmax, kw.newton, (int)kmax,
+                             nrhs, kw.iters, kw.status, st, kw.active, j));
+            KL(OVS_PROF_SMALL, 32.0 * j * nrhs,
+               launch_conv_check(kw.ccheck[1 - cbuf], kw.ccheck[cbuf], kmax, j, opts->tol, kw.active, kw.k_used,
+                                 kw.est, nrhs, st));
+            cbuf = 1 - cbuf;
+        }
         if (tma)
             KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
                launch_arnoldi_update_tma(basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
@@ -749,11 +784,154 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
        launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
                      w.yacc, N, units, plan, nrhs, nullptr, nullptr, st));
     KL(OVS_PROF_LAYOUT, bytes_layout(N, PREC_F64, nrhs), launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
-    if (!ydev) CK(cudaMemcpyAsync(y, yd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
+    (void)f64;
+    return OVS_OK;
+}
+
+static void remember_apply(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts, cudaStream_t st) {
     g->last_nrhs = nrhs;
     g->last_stream = st;
+    g->last_every = opts->check_every;
+    g->last_tol = opts->tol;
+    g->last_kmax = opts->k_max;
+}
+
+extern "C" {
+
+int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
+                   ovs_apply_info* info, void* stream) {
+    if (!x || !y) return fail(OVS_EINVAL, "NULL argument");
+    TRY(check_apply(g, nrhs, opts));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tp = tprec_of(opts->prec);
+    TRY(ensure_vec(g, nrhs, tp));
+    TRY(ensure_kry(g, nrhs, opts->k_max, tp));
+    const size_t f64 = field_bytes(g->N, PREC_F64);
+    const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+    const void* xd = x;
+    if (!xdev) {
+        CK(cudaMemcpyAsync(g->vw.sx, x, f64 * nrhs, cudaMemcpyHostToDevice, st));
+        xd = g->vw.sx;
+    }
+    void* yd = ydev ? y : g->vw.sy;
+    TRY(sign_apply_core(g, xd, yd, nrhs, opts, st));
+    if (!ydev) CK(cudaMemcpyAsync(y, yd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
+    remember_apply(g, nrhs, opts, st);
     if (info) return ovs_get_info(g, info, nrhs);
     if (!ydev) CK(cudaStreamSynchronize(st));
+    return OVS_OK;
+}
+
+}  // extern "C"
+
+// Recorded application of a handle for (nrhs, opts): sign_apply_core from
+// the staging buffers sx to sy, captured once on the handle's stream.
+static int get_graph(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts, ovs_gauge_s::GraphEntry** out) {
+    for (auto& e : g->graphs)
+        if (e.gen == g->gen && e.nrhs == nrhs && e.kmax == opts->k_max && e.prec == opts->prec &&
+            e.every == opts->check_every && e.tol == opts->tol) {
+            *out = &e;
+            return OVS_OK;
+        }
+    ovs_gauge_s::GraphEntry e;
+    e.nrhs = nrhs;
+    e.kmax = opts->k_max;
+    e.prec = opts->prec;
+    e.every = opts->check_every;
+    e.tol = opts->tol;
+    e.gen = g->gen;
+    long long l0[OVS_PROF_NCLASS];
+    double b0[OVS_PROF_NCLASS];
+    for (int c = 0; c < OVS_PROF_NCLASS; ++c) {
+        l0[c] = g->prof_launches[c];
+        b0[c] = g->prof_bytes[c];
+    }
+    CK(cudaStreamBeginCapture(g->istream, cudaStreamCaptureModeThreadLocal));
+    g->capturing = true;
+    const int rc = sign_apply_core(g, g->vw.sx, g->vw.sy, nrhs, opts, g->istream);
+    g->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(g->istream, &graph);
+    for (int c = 0; c < OVS_PROF_NCLASS; ++c) {  // counted at replay time instead
+        e.launches[c] = g->prof_launches[c] - l0[c];
+        e.bytes[c] = g->prof_bytes[c] - b0[c];
+        g->prof_launches[c] = l0[c];
+        g->prof_bytes[c] = b0[c];
+    }
+    if (rc < 0) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    CK(ec);
+    const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    g->graphs.push_back(e);
+    *out = &g->graphs.back();
+    return OVS_OK;
+}
+
+extern "C" {
+
+int ovs_sign_apply_batched(int32_t n, const ovs_gauge_t* gs, const void* const* x, void* const* y,
+                           const int32_t* nrhs, const ovs_apply_opts* opts, ovs_apply_info* info, void* stream) {
+    if (n <= 0 || !gs || !x || !y || !nrhs || !opts) return fail(OVS_EINVAL, "NULL argument or n <= 0");
+    for (int i = 0; i < n; ++i) {
+        if (!x[i] || !y[i]) return fail(OVS_EINVAL, "x[%d] or y[%d] is NULL", i, i);
+        for (int j = 0; j < i; ++j)
+            if (gs[j] == gs[i]) return fail(OVS_EINVAL, "handle %d appears twice (its buffers are not shared)", i);
+        TRY(check_apply(gs[i], nrhs[i], opts));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tp = tprec_of(opts->prec);
+    cudaEvent_t fork = nullptr;
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(fork, st);
+    bool any_host = false;
+    int rc = OVS_OK;
+    for (int i = 0; i < n && e == cudaSuccess && rc == OVS_OK; ++i) {
+        ovs_gauge_s* g = gs[i];
+        if ((rc = ensure_vec(g, nrhs[i], tp)) < 0) break;
+        if ((rc = ensure_kry(g, nrhs[i], opts->k_max, tp)) < 0) break;
+        if (!g->istream) e = cudaStreamCreateWithFlags(&g->istream, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !g->ev_join) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+        ovs_gauge_s::GraphEntry* ge = nullptr;
+        if ((rc = get_graph(g, nrhs[i], opts, &ge)) < 0) break;
+        const size_t bytes = field_bytes(g->N, PREC_F64) * nrhs[i];
+        const bool xdev = is_device_ptr(x[i]), ydev = is_device_ptr(y[i]);
+        any_host = any_host || !ydev;
+        e = cudaStreamWaitEvent(g->istream, fork, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->vw.sx, x[i], bytes, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                g->istream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge->exec, g->istream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(y[i], g->vw.sy, bytes, ydev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                g->istream);
+        if (e == cudaSuccess) e = cudaEventRecord(g->ev_join, g->istream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->ev_join, 0);
+        for (int c = 0; c < OVS_PROF_NCLASS; ++c) {
+            g->prof_launches[c] += ge->launches[c];
+            g->prof_bytes[c] += ge->bytes[c];
+        }
+        remember_apply(g, nrhs[i], opts, g->istream);
+    }
+    cudaEventDestroy(fork);
+    if (rc < 0) return rc;
+    CK(e);
+    if (info) {
+        int worst = OVS_OK, off = 0;
+        for (int i = 0; i < n; ++i) {
+            const int s = ovs_get_info(gs[i], info + off, nrhs[i]);
+            if (s < 0) return s;
+            if (s == OVS_ESIGN || worst == OVS_ESIGN) worst = OVS_ESIGN;
+            else if (s == OVS_NOT_CONVERGED) worst = OVS_NOT_CONVERGED;
+            off += nrhs[i];
+        }
+        return worst;
+    }
+    if (any_host) CK(cudaStreamSynchronize(st));
     return OVS_OK;
 }
 
@@ -762,7 +940,8 @@ int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
     if (nrhs <= 0 || nrhs > g->last_nrhs) return fail(OVS_EINVAL, "nrhs exceeds the last application");
     CK(cudaStreamSynchronize(g->last_stream));
     std::vector<int> ku(nrhs), it(nrhs), stt(nrhs);
-    std::vector<double> beta(nrhs);
+    std::vector<double> beta(nrhs), est(nrhs);
+    CK(cudaMemcpy(est.data(), g->kw.est, sizeof(double) * nrhs, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(ku.data(), g->kw.k_used, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(it.data(), g->kw.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(stt.data(), g->kw.status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost));
@@ -780,7 +959,11 @@ int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
         info[r].status = stt[r];
         info[r].reserved = 0;
         info[r].beta = beta[r];
-        info[r].est_err = 0.0;
+        info[r].est_err = est[r];
+        if (g->last_every > 0 && stt[r] == OVS_OK && !(est[r] < g->last_tol) && ku[r] >= g->last_kmax) {
+            stt[r] = OVS_NOT_CONVERGED;  // the estimate never reached tol within k_max
+            info[r].status = stt[r];
+        }
         if (stt[r] == OVS_ESIGN) worst = OVS_ESIGN;
         else if (stt[r] == OVS_NOT_CONVERGED && worst == OVS_OK) worst = OVS_NOT_CONVERGED;
     }
@@ -813,6 +996,9 @@ int ovs_profile_read(ovs_gauge_t g, double* ms, int64_t* launches, double* bytes
 void ovs_destroy(ovs_gauge_t g) {
     if (!g) return;
     prof_flush(g);
+    drop_graphs(g);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->istream) cudaStreamDestroy(g->istream);
     for (auto& e : g->events) cudaEventDestroy(e);
     free_deflation(g);
     free_vec(g->vw);

@@ -24,6 +24,8 @@ struct KryWork {  // Krylov basis and small matrices
     void* htmp = nullptr;        // [nrhs][jcap] complex128: reduced inner products of a sweep
     void* dcoef = nullptr;       // [nrhs] complex128
     int* err = nullptr;          // device error word (OVS_ETIMEOUT from bounded waits)
+    void* ccheck[2] = {nullptr, nullptr};  // [nrhs][kmax] coefficient vectors of successive checks
+    double* est = nullptr;                 // [nrhs] last convergence estimate
     void* partial = nullptr;     // [nrhs][nblk][jcap] complex128
     double* norm_part = nullptr; // [nrhs][nblk]
     double* beta = nullptr;
@@ -61,6 +63,8 @@ struct ovs_gauge_s {
     KryWork kw;
     int last_nrhs = 0;
     cudaStream_t last_stream = nullptr;
+    int last_every = 0, last_kmax = 0;
+    double last_tol = 0.0;
     // tracing (ovs_profile_*)
     struct Pending {
         int cls, ev;
@@ -72,6 +76,20 @@ struct ovs_gauge_s {
     std::vector<cudaEvent_t> events;
     std::vector<Pending> pending;
     cudaStream_t prof_stream = nullptr;
+    // batched form: recorded applications (CUDA graphs) and a private stream
+    struct GraphEntry {
+        int nrhs, kmax, prec, every;
+        double tol;
+        unsigned gen;
+        cudaGraphExec_t exec;
+        long long launches[OVS_PROF_NCLASS];
+        double bytes[OVS_PROF_NCLASS];
+    };
+    std::vector<GraphEntry> graphs;
+    unsigned gen = 1;  // bumped whenever buffers, mu or the deflation basis change
+    bool capturing = false;
+    cudaStream_t istream = nullptr;
+    cudaEvent_t ev_join = nullptr;
     // statistics of the last ovs_deflate_setup
     int setup_iters[2] = {0, 0};
     long long setup_matvecs = 0;

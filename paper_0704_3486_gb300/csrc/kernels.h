@@ -95,8 +95,13 @@ cudaError_t launch_sign_scale(const void* c, const double* sgn, int m, int nrhs,
 // ---- K3 (newton.cu)
 // coeff_r = beta_r * sgn(H_r[0:k,0:k]) e_1 with k = k_used[r], by Roberts'
 // iteration in FP64. work: 2 * nrhs * kmax * kmax complex128.
+// n_fixed > 0: use H[0:n_fixed, 0:n_fixed] instead of k_used[r]; right-hand
+// sides with active[r] == 0 are skipped when active != nullptr.
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
-                          int* status, cudaStream_t st);
+                          int* status, cudaStream_t st, const int* active = nullptr, int n_fixed = 0);
+// est[r] = ||cnew_r - cold_r|| / ||cnew_r||; below tol: active[r] = 0, k_used[r] = n
+cudaError_t launch_conv_check(const void* cnew, const void* cold, long long stride, int n, double tol, int* active,
+                              int* k_used, double* est, int nrhs, cudaStream_t st);
 
 }  // namespace ovs

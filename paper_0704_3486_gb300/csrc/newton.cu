@@ -128,10 +128,12 @@ __global__ void __launch_bounds__(NT) k_newton(const double2* __restrict__ H, lo
                                                const int* __restrict__ k_used, const double* __restrict__ beta,
                                                double2* __restrict__ coeff, long long coeff_stride,
                                                double2* __restrict__ work, int kmax, int* __restrict__ iters,
-                                               int* __restrict__ status) {
+                                               int* __restrict__ status, const int* __restrict__ active,
+                                               int n_fixed) {
     extern __shared__ unsigned char smem_raw[];
     const int r = blockIdx.x, tid = threadIdx.x;
-    const int n = k_used[r];
+    if (active != nullptr && active[r] == 0) return;
+    const int n = n_fixed > 0 ? n_fixed : k_used[r];
     cd* S = reinterpret_cast<cd*>(work) + (size_t)r * 2 * kmax * kmax;
     cd* T = S + (size_t)kmax * kmax;
     cd* colp = reinterpret_cast<cd*>(smem_raw);
@@ -233,7 +235,8 @@ __device__ __forceinline__ double cl_block_sum(double v, double* sh) {
 __global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
     k_newton_cluster(const double2* __restrict__ H, long long h_rhs_stride, int ldh, const int* __restrict__ k_used,
                      const double* __restrict__ beta, double2* __restrict__ coeff, long long coeff_stride,
-                     double2* __restrict__ work, int kmax, int* __restrict__ iters, int* __restrict__ status) {
+                     double2* __restrict__ work, int kmax, int* __restrict__ iters, int* __restrict__ status,
+                     const int* __restrict__ active, int n_fixed) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_piv[2], s_ok[2];
@@ -244,7 +247,8 @@ __global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
     const int c = (int)cl.block_rank();
     const int r = blockIdx.x / NCL;
     const int tid = threadIdx.x;
-    const int n = k_used[r];
+    if (active != nullptr && active[r] == 0) return;  // uniform over the cluster
+    const int n = n_fixed > 0 ? n_fixed : k_used[r];
     const int Wmax = (kmax + NCL - 1) / NCL;
     cd* T = reinterpret_cast<cd*>(smem_raw);          // [kmax][Wmax]
     cd* colp = T + (size_t)kmax * Wmax;              // [2][kmax] published pivot columns
@@ -427,6 +431,40 @@ __global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
     }
 }
 
+// Convergence estimate of the batched form (one block per right-hand side):
+// est = ||c_new - c_old|| / ||c_new|| over the coefficient vectors of two
+// checks (zero beyond their sizes); below tol the right-hand side stops with
+// k_used = n.
+__global__ void k_conv_check(const double2* __restrict__ cnew, const double2* __restrict__ cold, long long stride,
+                             int n, double tol, int* __restrict__ active, int* __restrict__ k_used,
+                             double* __restrict__ est) {
+    __shared__ double sh[33];
+    const int r = blockIdx.x;
+    if (active[r] == 0) return;
+    double d2 = 0.0, c2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 a = cnew[r * stride + i], b = cold[r * stride + i];
+        d2 += (a.x - b.x) * (a.x - b.x) + (a.y - b.y) * (a.y - b.y);
+        c2 += a.x * a.x + a.y * a.y;
+    }
+    d2 = blk_sum(d2, sh);
+    c2 = blk_sum(c2, sh);
+    if (threadIdx.x == 0) {
+        const double e = c2 > 0.0 ? sqrt(d2 / c2) : 0.0;
+        est[r] = e;
+        if (e < tol) {
+            active[r] = 0;
+            k_used[r] = n;
+        }
+    }
+}
+
+cudaError_t launch_conv_check(const void* cnew, const void* cold, long long stride, int n, double tol, int* active,
+                              int* k_used, double* est, int nrhs, cudaStream_t st) {
+    k_conv_check<<<nrhs, 256, 0, st>>>((const double2*)cnew, (const double2*)cold, stride, n, tol, active, k_used, est);
+    return cudaGetLastError();
+}
+
 static size_t cluster_smem(int kmax) {
     const int Wmax = (kmax + NCL - 1) / NCL;
     return ((size_t)kmax * Wmax + 3 * (size_t)kmax + Wmax) * sizeof(cd) + 2 * (size_t)kmax * sizeof(int);
@@ -434,7 +472,7 @@ static size_t cluster_smem(int kmax) {
 
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
-                          int* status, cudaStream_t st) {
+                          int* status, cudaStream_t st, const int* active, int n_fixed) {
     const size_t need = cluster_smem(kmax);
     if (kmax <= kClusterMaxN && need <= 220 * 1024) {
         static size_t attr_set = 0;  // dynamic shared memory opted in so far
@@ -446,7 +484,7 @@ cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const 
         }
         k_newton_cluster<<<nrhs * NCL, NTC, need, st>>>(
             (const double2*)H, h_rhs_stride, ldh, k_used, beta, (double2*)coeff, coeff_stride, (double2*)work, kmax,
-            iters, status);
+            iters, status, active, n_fixed);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)kmax * 2 * sizeof(cd) + (size_t)kmax * sizeof(int);
@@ -457,7 +495,7 @@ cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const 
         attr = true;
     }
     k_newton<<<nrhs, NT, smem, st>>>((const double2*)H, h_rhs_stride, ldh, k_used, beta, (double2*)coeff,
-                                     coeff_stride, (double2*)work, kmax, iters, status);
+                                     coeff_stride, (double2*)work, kmax, iters, status, active, n_fixed);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,137 @@
+"""Convergence-stopped applications (A7) and the batched multi-instance form.
+
+A7: every `check_every` steps the GPU forms c_j = beta sgn(H_j) e_1 and stops
+a right-hand side once ||c_j - c_{j-every}|| / ||c_j|| < tol; the oracle's
+arnoldi_sign_adaptive does the same on the CPU. Batched: several handles of
+different lattice sizes, mu and right-hand-side counts in one call; every
+instance must equal its single-instance result and the oracle.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import arnoldi, deflation, lattice, signfun
+
+pytestmark = pytest.mark.gpu
+
+MW = -1.5
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_convergence_stop_matches_oracle(gpu):
+    dims, mu = (4, 4, 4, 4), 0.3
+    links = synth.gauge_links(dims, 1, 0.5)
+    h = lattice.hw_operator(links, dims, mu, MW)
+    g = gpu.create_gauge_from_links(dims, links, gpu.MIXED)
+    gpu.set_mu(g, mu, MW)
+    x = synth.gaussian_vectors(3072, 3, 21)
+    x[2] = synth.ones_vector(3072)[0] / np.sqrt(3072)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    st, info = gpu.sign_apply(g, xd, yd, 300, prec=gpu.F64, check_every=10, tol=1e-4)
+    y = yd.cpu().numpy()
+    for r in range(3):
+        ref, oinfo = arnoldi.arnoldi_sign_adaptive(lambda q: h @ q, x[r], 300, 10, 1e-4)
+        assert info[r]["k_used"] == oinfo["k_used"]
+        assert info[r]["k_used"] % 10 == 0 and info[r]["k_used"] < 300
+        assert info[r]["est_err"] < 1e-4 and info[r]["status"] == 0
+        assert rel(y[r], ref) < 1e-12
+    # mixed form: same stopping rule, result within 1e-6 of the FP64 oracle at its k
+    st, info = gpu.sign_apply(g, xd, yd, 300, prec=gpu.MIXED, check_every=10, tol=1e-4)
+    y = yd.cpu().numpy()
+    for r in range(3):
+        ref, _ = arnoldi.arnoldi_sign(lambda q: h @ q, x[r], info[r]["k_used"])
+        assert rel(y[r], ref) < 1e-6
+    g.destroy()
+
+
+def test_convergence_not_reached_is_flagged(gpu):
+    dims, mu = (4, 4, 4, 4), 0.3
+    g = gpu.create_gauge(dims, 1, 0.5, gpu.F64)
+    gpu.set_mu(g, mu, MW)
+    xd = torch.from_numpy(synth.gaussian_vectors(3072, 1, 5)).cuda()
+    yd = torch.empty_like(xd)
+    st, info = gpu.sign_apply(g, xd, yd, 40, prec=gpu.F64, check_every=10, tol=1e-12)
+    assert st == 1 and info[0]["status"] == 1 and info[0]["k_used"] == 40
+    with pytest.raises(gpu.OvsError, match="EINVAL"):
+        gpu.sign_apply(g, xd, yd, 40, prec=gpu.F64, check_every=3, tol=1e-6)
+    g.destroy()
+
+
+def _instance(gpu, dims, seed, eps, mu, nrhs, m):
+    v = int(np.prod(dims))
+    links = synth.gauge_links(dims, seed, eps)
+    h = lattice.hw_operator(links, dims, mu, MW)
+    g = gpu.create_gauge_from_links(dims, links, gpu.MIXED)
+    gpu.set_mu(g, mu, MW)
+    defl = None
+    if m:
+        lam, R, L = deflation.critical_pairs_dense(h.toarray(), m)
+        gpu.deflate_load(g, R.T.copy(), L.T.copy(), lam)
+        defl = (R, L, lam)
+    x = synth.gaussian_vectors(12 * v, nrhs, seed + 100)
+    return g, h, x, defl
+
+
+def test_batched_instances_match_single_and_oracle(gpu):
+    specs = [((4, 4, 4, 4), 1, 0.5, 0.1, 2, 0), ((2, 4, 4, 4), 2, 0.7, 0.2, 1, 8),
+             ((4, 4, 6, 4), 3, 0.6, 0.3, 3, 0), ((2, 2, 4, 4), 4, 0.55, 0.2, 2, 6)]
+    inst = [_instance(gpu, *sp) for sp in specs]
+    xs = [torch.from_numpy(x).cuda() for (_, _, x, _) in inst]
+    ys = [torch.empty_like(x) for x in xs]
+    for prec, tol in ((gpu.F64, 1e-12), (gpu.MIXED, 1e-6)):
+        st, info = gpu.sign_apply_batched([i[0] for i in inst], xs, ys, 60, prec=prec)
+        assert st == 0 and len(info) == sum(x.shape[0] for x in xs)
+        for (g, h, x, defl), xd, yd in zip(inst, xs, ys):
+            y_single = torch.empty_like(xd)
+            gpu.sign_apply(g, xd, y_single, 60, prec=prec)
+            assert torch.equal(yd, y_single)  # same kernels, same order
+            for r in range(x.shape[0]):
+                if defl is None:
+                    ref, _ = arnoldi.arnoldi_sign(lambda q: h @ q, x[r], 60)
+                else:
+                    ref, _ = deflation.lr_sign_apply(lambda q: h @ q, x[r], defl[0], defl[1], defl[2], 60)
+                assert rel(yd.cpu().numpy()[r], ref) < tol
+    for i in inst:
+        i[0].destroy()
+
+
+def test_batched_replay_and_rerecord(gpu):
+    specs = [((4, 4, 4, 4), 5, 0.5, 0.2, 2, 0), ((2, 4, 4, 4), 6, 0.6, 0.1, 1, 0)]
+    inst = [_instance(gpu, *sp) for sp in specs]
+    gs = [i[0] for i in inst]
+    xs = [torch.from_numpy(i[2]).cuda() for i in inst]
+    ys1 = [torch.empty_like(x) for x in xs]
+    ys2 = [torch.empty_like(x) for x in xs]
+    gpu.sign_apply_batched(gs, xs, ys1, 40, prec=gpu.MIXED, check_every=10, tol=1e-5)
+    gpu.sign_apply_batched(gs, xs, ys2, 40, prec=gpu.MIXED, check_every=10, tol=1e-5)  # replay
+    for a, b in zip(ys1, ys2):
+        assert torch.equal(a, b)
+    # a new mu drops the recorded application: the result follows the new operator
+    gpu.set_mu(gs[0], 0.3, MW)
+    gpu.sign_apply_batched(gs, xs, ys2, 40, prec=gpu.F64)
+    links = synth.gauge_links((4, 4, 4, 4), 5, 0.5)
+    h = lattice.hw_operator(links, (4, 4, 4, 4), 0.3, MW)
+    ref, _ = arnoldi.arnoldi_sign(lambda q: h @ q, inst[0][2][0], 40)
+    assert rel(ys2[0].cpu().numpy()[0], ref) < 1e-12
+    # host buffers
+    xh = [i[2] for i in inst]
+    yh = [np.empty_like(x) for x in xh]
+    gpu.sign_apply_batched(gs, xh, yh, 40, prec=gpu.F64)
+    assert np.array_equal(yh[0], ys2[0].cpu().numpy())
+    for g in gs:
+        g.destroy()
+
+
+def test_batched_errors(gpu):
+    g = gpu.create_gauge((2, 2, 2, 2), 1, 0.5, gpu.F64)
+    gpu.set_mu(g, 0.1, MW)
+    x = torch.zeros((1, 192), dtype=torch.complex128, device="cuda:0")
+    with pytest.raises(gpu.OvsError, match="twice"):
+        gpu.sign_apply_batched([g, g], [x, x], [x.clone(), x.clone()], 4, prec=gpu.F64)
+    g.destroy()

@@ -325,3 +325,16 @@ def test_hermitian_deflation_special_case():
     y_k, _ = arnoldi.arnoldi_sign(lambda z: h @ z, x_perp, 60)
     y2 = u @ (np.sign(lam[order]) * (u.conj().T @ x)) + y_k
     assert rel(y1, y2) < 1e-12
+
+
+def test_adaptive_stops_and_matches_fixed_k():
+    """The convergence-stopped Arnoldi returns the fixed-k result at its k."""
+    h, n = _small_problem()
+    x = synth.gaussian_vectors(n, 1, 2)[0]
+    y, info = arnoldi.arnoldi_sign_adaptive(lambda q: h @ q, x, 300, 10, 1e-4)
+    assert info["k_used"] % 10 == 0 and info["k_used"] < 300 and info["est"] < 1e-4
+    y_fix, _ = arnoldi.arnoldi_sign(lambda q: h @ q, x, info["k_used"])
+    assert rel(y, y_fix) < 1e-13
+    # the estimate tracks the true change: the error vs the dense sign is small
+    ref = signfun.sgn_apply_dense(h.toarray(), x)
+    assert rel(y, ref) < 1e-2
