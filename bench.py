@@ -334,11 +334,11 @@ def run_ours(args, w, world, rank, local):
     # class (16^3x32, 2 RHS, J = 30; profiles/) gave traffic / algorithmic
     # bytes; traffic grows in proportion to the vectors read, so a launch of
     # the timed step moves that ratio times its algorithmic bytes.
-    traffic_ratio = {"dots": 808.25 / 805.31, "update": 850.60 / 855.64}.get(top)
+    traffic_ratio = {"dots": 808.94 / 805.31, "update": 850.60 / 855.64}.get(top)
     per_launch = prof[top]["bytes"] / max(prof[top]["launches"], 1)
     traffic = round(per_launch * traffic_ratio) if traffic_ratio else None
     share = {c: round(prof[c]["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-9), 4) for c in prof}
-    roofline = {"bound": "hbm", "kernel": {"dots": "k_dots (CGS2 inner products)",
+    roofline = {"bound": "hbm", "kernel": {"dots": "k_gdots2_ws (CGS2 inner products)",
                                             "update": "k_update (CGS2 update / recombination)",
                                             "matvec": "k_wilson (H_w stencil)"}[top],
                 "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),

@@ -213,7 +213,9 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     const int jneed = std::max(gdots_stride(2, kmax), gdots_stride(1, std::max(kmax, g->m)));
     const BlasPlan plan = blas_plan(field_units(g->N, tprec), nrhs, g->num_sms);
     const BlasPlan plan1 = blas_plan(field_units(g->N, tprec), 1, g->num_sms);
-    const int nblk_need = std::max(plan.nblk, plan1.nblk);
+    const int nblk_need =
+        std::max(std::max(plan.nblk, plan1.nblk),
+                 tprec == PREC_F32 ? gdots_chunk_slots(field_units(g->N, tprec), nrhs, g->num_sms) : 0);
     if (k.prec == tprec && k.nrhs >= nrhs && k.kmax >= kmax && k.jcap >= jneed && k.nblk >= nblk_need) return OVS_OK;
     const bool same = (k.prec == tprec);
     const int n = std::max(nrhs, same ? k.nrhs : 0);
@@ -691,6 +693,7 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
     const long long h_rhs = (long long)(kmax + 1) * kmax;
     const BlasPlan plan = blas_plan(units, nrhs, g->num_sms);
     const BlasPlan plan64 = blas_plan(N, nrhs, g->num_sms);
+    const int dslots = tp == PREC_F32 ? gdots_chunk_slots(units, nrhs, g->num_sms) : 0;
     char* basis = (char*)kw.basis;
 
     // input, canonical complex128 -> internal precision
@@ -735,11 +738,18 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
            launch_wilson(tp, true, links_for(g, tp), w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
                          kw.active, st));
         const bool tma = (tp == PREC_F32) && tma_update_fits(j);
-        KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (j + 2.0),
-           launch_gdots(tp, 2, basis, basis_rhs_units, units, j, w.xint, units, w.wvec, units, true, units, plan, nrhs,
-                        kw.partial, kw.active, st));
-        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
-           launch_reduce(kw.partial, plan.nblk, S, S, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
+        const bool chunked = (tp == PREC_F32) && gdots_chunk_fits(j);
+        const int dblk = chunked ? dslots : plan.nblk;
+        if (chunked)
+            KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (j + 2.0),
+               launch_gdots2_chunk(basis, basis_rhs_units, units, j, w.xint, units, w.wvec, units, units, nrhs,
+                                   g->num_sms, dslots, kw.partial, kw.active, kw.err, st));
+        else
+            KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (j + 2.0),
+               launch_gdots(tp, 2, basis, basis_rhs_units, units, j, w.xint, units, w.wvec, units, true, units, plan,
+                            nrhs, kw.partial, kw.active, st));
+        KL(OVS_PROF_SMALL, 16.0 * dblk * S * nrhs,
+           launch_reduce(kw.partial, dblk, S, S, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
         KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 3.0 * j) * nrhs,
            launch_arnoldi_step(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.beta, kw.inv_beta, kw.dcoef, kw.hnorm2,
                                kw.active, kw.k_used, nrhs, st));

@@ -176,13 +176,16 @@ struct Axpy {
 
 // out_r = [gamma5] (in_r - kappa * hops(in_r)) for r = blockIdx.y.
 // in/out strides are in bytes between right-hand sides.
+// Grid: x = right-hand side (fastest), y = tile of 128 sites, so the blocks
+// of all right-hand sides that share a tile of links run back to back and
+// read the links from L2 rather than once per right-hand side from DRAM.
 template <typename R, bool G5, bool AX = false>
 __global__ void __launch_bounds__(128) k_wilson(const void* __restrict__ links, const char* __restrict__ in,
                                                 char* out, size_t in_stride, size_t out_stride, Geom g,
                                                 R kappa, R emu, R emmu, const int* __restrict__ active,
                                                 Axpy ax = Axpy{}) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
+    const int s = blockIdx.y * blockDim.x + threadIdx.x;
+    const int r = blockIdx.x;
     if (s >= g.V) return;
     if (active != nullptr && active[r] == 0) return;
     const void* inr = in + r * in_stride;
@@ -307,11 +310,13 @@ __global__ void k_links_to_canonical(const double2* __restrict__ u64, double2* _
 // ------------------------------------------------------------- host launch
 static inline dim3 site_grid(int V, int nrhs, int threads) { return dim3((V + threads - 1) / threads, nrhs); }
 
+static inline dim3 rhs_site_grid(int V, int nrhs, int threads) { return dim3(nrhs, (V + threads - 1) / threads); }
+
 cudaError_t launch_wilson(int prec, bool gamma5, const void* links, const void* in, size_t in_stride, void* out,
                           size_t out_stride, const Geom& g, int nrhs, double kappa, double mu, const int* active,
                           cudaStream_t st) {
     const int T = 128;
-    dim3 grid = site_grid(g.V, nrhs, T);
+    dim3 grid = rhs_site_grid(g.V, nrhs, T);
     const double emu = exp(mu), emmu = exp(-mu);
     if (prec == PREC_F64) {
         if (gamma5)
@@ -336,7 +341,7 @@ cudaError_t launch_wilson_axpy(int prec, const void* links, const void* in, size
                                double by, double ah, const Geom& g, int nrhs, double kappa, double mu,
                                cudaStream_t st) {
     const int T = 128;
-    dim3 grid = site_grid(g.V, nrhs, T);
+    dim3 grid = rhs_site_grid(g.V, nrhs, T);
     const double emu = exp(mu), emmu = exp(-mu);
     Axpy ax{(const char*)X, xs, bx, (const char*)Y, ys, by, ah};
     if (prec == PREC_F64)

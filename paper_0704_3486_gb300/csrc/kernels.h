@@ -83,6 +83,15 @@ cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, v
 // TMA-pipelined complex64 form of the Arnoldi update sweep (tma_sweeps.cu);
 // *err receives OVS_ETIMEOUT if a bounded wait gives up.
 bool tma_update_fits(int J);
+// persistent TMA inner-product sweep (complex64, NW = 2): one block per SM
+// over row chunks of 2048 units; partial[r][slot][2J + 2] for
+// slot < gdots_chunk_slots(nunits, nrhs, num_sms)
+bool gdots_chunk_fits(int J);
+int gdots_chunk_slots(long long nunits, int nrhs, int num_sms);
+cudaError_t launch_gdots2_chunk(const void* basis, long long basis_rhs_stride, long long vec_stride, int J,
+                                const void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
+                                long long nunits, int nrhs, int num_sms, int nslot, void* partial, const int* active,
+                                int* err, cudaStream_t st);
 cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, long long vec_stride, int J,
                                       const void* red, long long red_stride, const double* inv_beta,
                                       const void* dcoef, void* u, long long u_rhs_stride, const void* z,

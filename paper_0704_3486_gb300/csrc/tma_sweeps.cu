@@ -104,6 +104,319 @@ __device__ void drain(int idx, int total, uint64_t* full, int* err) {
 
 }  // namespace
 
+// Inner products of the delayed-reorthogonalisation Arnoldi step, complex64
+// basis: s_i = V_i^H u, t_i = V_i^H z (i < J), u^H u and u^H z.
+//
+// Persistent, warp-specialised form, one block per SM: 8 consumer warps and
+// one producer warp. The work items are the row chunks of CU = 2048 units of
+// every right-hand side, flattened as (r, c) and split into one contiguous
+// range per block. For each chunk a consumer thread holds its 8 units of u
+// and of z in registers; the basis streams through DS = 3 stages (192 KB in
+// flight) of 8 vectors x 512 units, groups of 8 vectors in the outer order
+// and the 4 tiles of the chunk inside, so a thread keeps its products of one
+// group in registers across the 4 stages (16 complex terms per vector,
+// FP32). A warp transpose-reduction then leaves one (item, component) per
+// lane; the 8 warps' partials (512 terms each) are summed in FP64 into the
+// block's accumulators.
+//
+// Stage hand-off uses mbarriers only: `full[s]` completes when the copies of
+// stage s have landed (transaction bytes), `empty[s]` when all 8 consumer
+// warps have read it. The producer (one lane) refills a stage as soon as it
+// is released, so consumer warps run up to DS stages apart and none of them
+// waits for the copy issue. The consumers meet on a named barrier once per
+// group of 8 vectors, where they also agree on any timed-out wait.
+//
+// Output: the partial sums of right-hand side r go to partial[r][slot][2J+2]
+// (layout of k_gdots with NW = 2, slot = block - first block of r); a block
+// that starts r also zeroes r's slots beyond its last one, so every one of
+// the `nslot` slots is defined.
+namespace {
+constexpr int CU = 2048;                     // units per row chunk
+constexpr int DU = 512;                      // units per tile
+constexpr int DE = DU / TB;                  // units per consumer thread per tile
+constexpr int DNT = CU / DU;                 // tiles per chunk
+constexpr int DS = 3;                        // stages
+constexpr int DTHREADS = TB + 32;            // consumer warps + producer warp
+constexpr size_t kDStage = (size_t)TG * DU * 16;
+
+template <int CUR, int O>
+__device__ __forceinline__ void tstep32(float (&v)[32], bool upper) {
+#pragma unroll
+    for (int i = 0; i < CUR / 2; ++i) {
+        const float send = upper ? v[i] : v[i + CUR / 2];
+        const float keep = upper ? v[i + CUR / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+__device__ __forceinline__ double wsum_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// named barrier 1 over the TB consumer threads; the OR of `p` over them
+__device__ __forceinline__ bool consumers_sync_or(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 1, %2, a;\n selp.u32 %0, 1, 0, b;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "n"(TB)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TB) : "memory"); }
+// bounded wait that also gives up once another thread has raised `abort`
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    for (long long n = 0; n < kWaitLimit; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+// block that owns flattened item i under the contiguous split of T items
+// over G blocks (block q owns [floor(qT/G), floor((q+1)T/G)))
+__host__ __device__ inline int owner_of(long long i, long long T, int G) {
+    return (int)(((i + 1) * G - 1) / T);
+}
+__host__ __device__ inline long long range_lo(int q, long long T, int G) { return (long long)q * T / G; }
+}  // namespace
+
+__global__ void __launch_bounds__(DTHREADS, 1)
+    k_gdots2_ws(const float4* __restrict__ basis, long long basis_rhs_stride, long long vec_stride, int J,
+                const float4* __restrict__ u, long long u_rhs_stride, const float4* __restrict__ z,
+                long long z_rhs_stride, long long nunits, int nrhs, int nslot, double2* __restrict__ partial,
+                const int* __restrict__ active, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[DS];
+    __shared__ __align__(8) uint64_t empty[DS];
+    __shared__ float scratch[2][TW][32];
+    __shared__ double sx[TW][3];
+    __shared__ int abort_flag;
+    double* acc = reinterpret_cast<double*>(smem + DS * kDStage);  // [2J + 2][2]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, q = blockIdx.x;
+    const int S = 2 * J + 2;
+    const long long cpr = (nunits + CU - 1) / CU;  // chunks per right-hand side
+    const long long T = cpr * nrhs;
+    const long long lo = range_lo(q, T, G), hi = range_lo(q + 1, T, G);
+    const int ngroups = (J + TG - 1) / TG;
+    volatile int* abort = &abort_flag;
+    if (tid == 0) {
+        for (int k = 0; k < DS; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], TW);
+        }
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == TW) {  // ---- producer warp: one lane issues every stage
+        if (lane != 0 || ngroups == 0) return;
+        int n = 0;  // stages issued
+        bool ok = true;
+        for (long long it = lo; it < hi && ok; ++it) {
+            const long long r = it / cpr, c = it - r * cpr;
+            if (active != nullptr && active[r] == 0) continue;
+            const long long u0 = c * CU;
+            const int len = (int)min((long long)CU, nunits - u0);
+            const float4* Vr = basis + r * basis_rhs_stride + u0;
+            for (int g = 0; g < ngroups && ok; ++g) {
+                const int nv = min(TG, J - g * TG);
+                for (int t = 0; t < DNT; ++t) {
+                    const int s = n % DS;
+                    if (n >= DS) {  // the consumers' release of this stage's previous use
+                        if (!mbar_wait_or_abort(&empty[s], (uint32_t)((n / DS - 1) & 1), abort)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_proxy_async_smem();
+                    }
+                    const int units = min(DU, len - t * DU);
+                    if (units <= 0) {  // tile beyond a short chunk: complete the phase without bytes
+                        mbar_expect_tx(&full[s], 0);
+                    } else {
+                        const uint32_t bytes = (uint32_t)units * 16u;
+                        unsigned char* dst = smem + (size_t)s * kDStage;
+                        mbar_expect_tx(&full[s], bytes * nv);
+                        for (int v = 0; v < nv; ++v)
+                            bulk_load(dst + (size_t)v * DU * 16, Vr + (long long)(g * TG + v) * vec_stride + t * DU,
+                                      bytes, &full[s]);
+                    }
+                    ++n;
+                }
+            }
+        }
+        // the block's shared memory must outlive every copy: wait until the
+        // consumers have released the last stages, or, if they gave up, until
+        // the copies still in flight have landed (bounded)
+        for (int k = max(0, n - DS); k < n && ok; ++k)
+            ok = mbar_wait_or_abort(&empty[k % DS], (uint32_t)((k / DS) & 1), abort);
+        if (!ok) {
+            atomicExch(err, OVS_ETIMEOUT_CODE);
+            abort_flag = 1;
+            for (int k = max(0, n - DS); k < n; ++k) mbar_wait_bounded(&full[k % DS], (uint32_t)((k / DS) & 1));
+        }
+        return;
+    }
+
+    // ---- consumer warps
+    // zero this block's share of the unused slots: the block owning the first
+    // chunk of r clears r's slots past the last block that works on r
+    for (long long r = 0; r < nrhs; ++r) {
+        if (owner_of(r * cpr, T, G) != q) continue;
+        const int used = owner_of((r + 1) * cpr - 1, T, G) - q + 1;
+        double* base = reinterpret_cast<double*>(partial + ((size_t)r * nslot) * S);
+        for (long long i = (long long)used * 2 * S + tid; i < (long long)nslot * 2 * S; i += TB) base[i] = 0.0;
+    }
+    int n = 0;   // stages consumed
+    int gg = 0;  // groups completed, over all chunks (selects the scratch buffer)
+    long long seg_r = -1;
+    bool bad = false;
+    double ea = 0.0, ebr = 0.0, ebi = 0.0;  // u^H u, u^H z of the segment (per thread)
+
+    auto flush = [&](long long r) {
+        ea = wsum_d(ea);
+        ebr = wsum_d(ebr);
+        ebi = wsum_d(ebi);
+        if (lane == 0) {
+            sx[warp][0] = ea;
+            sx[warp][1] = ebr;
+            sx[warp][2] = ebi;
+        }
+        ea = ebr = ebi = 0.0;
+        consumers_sync();
+        if (tid == 0) {
+            double a = 0.0, br = 0.0, bi = 0.0;
+            for (int w = 0; w < TW; ++w) {
+                a += sx[w][0];
+                br += sx[w][1];
+                bi += sx[w][2];
+            }
+            acc[(2 * J) * 2] = a;
+            acc[(2 * J) * 2 + 1] = 0.0;
+            acc[(2 * J + 1) * 2] = br;
+            acc[(2 * J + 1) * 2 + 1] = bi;
+        }
+        consumers_sync();
+        const int slot = q - owner_of(r * cpr, T, G);
+        double* out = reinterpret_cast<double*>(partial + ((size_t)r * nslot + slot) * S);
+        for (int i = tid; i < 2 * S; i += TB) out[i] = acc[i];
+        consumers_sync();
+    };
+
+    for (long long it = lo; it < hi; ++it) {
+        const long long r = it / cpr, c = it - r * cpr;
+        if (active != nullptr && active[r] == 0) continue;
+        if (r != seg_r) {
+            if (seg_r >= 0) flush(seg_r);
+            for (int i = tid; i < 2 * S; i += TB) acc[i] = 0.0;
+            seg_r = r;
+        }
+        const long long u0 = c * CU;
+        const int len = (int)min((long long)CU, nunits - u0);
+        float4 ur[DNT * DE], zr[DNT * DE];
+        const float4* up = u + r * u_rhs_stride + u0;
+        const float4* zp = z + r * z_rhs_stride + u0;
+#pragma unroll
+        for (int k = 0; k < DNT * DE; ++k) {
+            const int p = k * TB + tid;  // tile k / DE, unit (k % DE) * TB + tid of it
+            ur[k] = p < len ? up[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+            zr[k] = p < len ? zp[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < DNT * DE; ++k) {
+            cf uc[2], zc[2];
+            Unit<float>::split(ur[k], uc);
+            Unit<float>::split(zr[k], zc);
+            cf aa = {0.f, 0.f}, bz = {0.f, 0.f};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                cfmac(aa, uc[h], uc[h]);
+                cfmac(bz, uc[h], zc[h]);
+            }
+            ea += aa.re;
+            ebr += bz.re;
+            ebi += bz.im;
+        }
+        for (int g = 0; g < ngroups; ++g) {
+            float v[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) v[k] = 0.f;
+            const int nv = min(TG, J - g * TG);
+#pragma unroll
+            for (int t = 0; t < DNT; ++t) {
+                const int s = n % DS;
+                const bool got = bad || mbar_wait_or_abort(&full[s], (uint32_t)((n / DS) & 1), abort);
+                if (!__all_sync(0xffffffffu, got)) {  // keep `bad` uniform over the warp
+                    if (lane == 0) {
+                        atomicExch(err, OVS_ETIMEOUT_CODE);
+                        abort_flag = 1;
+                    }
+                    bad = true;
+                }
+                if (!bad) {
+                    const float4* st4 = reinterpret_cast<const float4*>(smem + (size_t)s * kDStage);
+#pragma unroll
+                    for (int e = 0; e < DE; ++e) {
+                        const int k = t * DE + e;
+                        if (k * TB + tid < len) {
+                            cf uc[2], zc[2];
+                            Unit<float>::split(ur[k], uc);
+                            Unit<float>::split(zr[k], zc);
+#pragma unroll
+                            for (int gi = 0; gi < TG; ++gi) {
+                                if (gi < nv) {
+                                    cf vc[2];
+                                    Unit<float>::split(st4[gi * DU + e * TB + tid], vc);
+#pragma unroll
+                                    for (int h = 0; h < 2; ++h) {
+                                        cf a = {v[2 * gi], v[2 * gi + 1]};
+                                        cfmac(a, vc[h], uc[h]);
+                                        v[2 * gi] = a.re;
+                                        v[2 * gi + 1] = a.im;
+                                        cf bz = {v[2 * (TG + gi)], v[2 * (TG + gi) + 1]};
+                                        cfmac(bz, vc[h], zc[h]);
+                                        v[2 * (TG + gi)] = bz.re;
+                                        v[2 * (TG + gi) + 1] = bz.im;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+                }
+                ++n;
+            }
+            // group complete: warp partials of the 8 vectors, lane l holding
+            // item l/2 = which * 8 + gi, component l % 2
+            tstep32<32, 16>(v, (lane & 16) != 0);
+            tstep32<16, 8>(v, (lane & 8) != 0);
+            tstep32<8, 4>(v, (lane & 4) != 0);
+            tstep32<4, 2>(v, (lane & 2) != 0);
+            tstep32<2, 1>(v, (lane & 1) != 0);
+            scratch[gg & 1][warp][lane] = v[0];
+            // all consumers leave together; the producer waits for the copies
+            if (consumers_sync_or(bad)) return;
+            if (warp == 0) {
+                double sum = 0.0;
+#pragma unroll
+                for (int w = 0; w < TW; ++w) sum += (double)scratch[gg & 1][w][lane];
+                const int item = lane >> 1, comp = lane & 1;
+                const int which = item / TG, gi = item - which * TG;
+                if (gi < nv) acc[(which * J + g * TG + gi) * 2 + comp] += sum;
+            }
+            // this buffer is next written at the end of the group after the
+            // next one, behind a barrier that warp 0 reaches only now
+            ++gg;
+        }
+    }
+    if (seg_r >= 0) flush(seg_r);
+}
+
 // Update sweep of the delayed-reorthogonalisation Arnoldi step, complex64:
 //   v_J = (u - sum_i V_i s_i) / beta -> basis slot J,
 //   u   <- (z - sum_i V_i t_i) / beta - v_J d
@@ -203,6 +516,44 @@ __global__ void __launch_bounds__(TB, 1)
 }
 
 bool tma_update_fits(int J) { return TNS * kStageBytes + (size_t)(2 * J + 1) * sizeof(cf) <= 220 * 1024; }
+
+static size_t gdots_chunk_smem(int J) { return DS * kDStage + (size_t)(2 * J + 2) * 16; }
+
+bool gdots_chunk_fits(int J) { return gdots_chunk_smem(J) <= 222 * 1024; }
+
+static int gdots_chunk_grid(long long nunits, int nrhs, int num_sms) {
+    const long long T = (nunits + CU - 1) / CU * nrhs;
+    return (int)std::max<long long>(1, std::min<long long>(num_sms, T));
+}
+
+int gdots_chunk_slots(long long nunits, int nrhs, int num_sms) {
+    const long long cpr = (nunits + CU - 1) / CU, T = cpr * nrhs;
+    const int G = gdots_chunk_grid(nunits, nrhs, num_sms);
+    int n = 1;
+    for (long long r = 0; r < nrhs; ++r)
+        n = std::max(n, owner_of((r + 1) * cpr - 1, T, G) - owner_of(r * cpr, T, G) + 1);
+    return n;
+}
+
+cudaError_t launch_gdots2_chunk(const void* basis, long long basis_rhs_stride, long long vec_stride, int J,
+                                const void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
+                                long long nunits, int nrhs, int num_sms, int nslot, void* partial, const int* active,
+                                int* err, cudaStream_t st) {
+    static size_t set = 0;
+    const size_t smem = gdots_chunk_smem(J);
+    if (smem > set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_gdots2_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    if (nslot != gdots_chunk_slots(nunits, nrhs, num_sms)) return cudaErrorInvalidValue;
+    const int G = gdots_chunk_grid(nunits, nrhs, num_sms);
+    k_gdots2_ws<<<G, DTHREADS, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J, (const float4*)u,
+                                           u_rhs_stride, (const float4*)z, z_rhs_stride, nunits, nrhs, nslot,
+                                           (double2*)partial, active, err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, long long vec_stride, int J,
                                       const void* red, long long red_stride, const double* inv_beta,
