@@ -121,6 +121,54 @@ def wilson_dirac(links, dims, mu, m_w, convention="baseline"):
     return d
 
 
+def wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention="baseline"):
+    """(D_w(mu) x) at the listed sites only, as an array (len(sites), 12).
+
+    Each of the eight hops of Eq. Dw is summed directly for the requested
+    sites, without forming the matrix, so that lattices too large for the
+    sparse form (16^3 x 32: N = 1.57 M) can still be checked site by site.
+    Same readings as ``wilson_dirac``.
+    """
+    dims = tuple(int(d) for d in dims)
+    lx, ly, lz, lt = dims
+    sites = np.asarray(sites, dtype=np.int64)
+    if convention not in ("baseline", "paper"):
+        raise ValueError("convention must be 'baseline' or 'paper'")
+    sign_fwd = -1.0 if convention == "baseline" else +1.0
+    kappa = kappa_of(m_w)
+    gam = gamma_matrices()
+    one = np.eye(4, dtype=np.complex128)
+    psi = np.asarray(x, dtype=np.complex128).reshape(-1, 4, 3)
+    coord = [sites % lx, (sites // lx) % ly, (sites // (lx * ly)) % lz, sites // (lx * ly * lz)]
+    out = psi[sites].copy()
+    for nu in range(4):
+        tfac = np.exp(mu) if nu == 3 else 1.0
+        for step in (+1, -1):
+            c = [a.copy() for a in coord]
+            raw = coord[nu] + step
+            wrapped = (raw < 0) | (raw >= dims[nu])
+            c[nu] = raw % dims[nu]
+            nb = ((c[3] * lz + c[2]) * ly + c[1]) * lx + c[0]
+            bc = np.where(wrapped & (nu == 3), -1.0, 1.0)
+            if step > 0:  # psi(s + nu) through U_nu(s), (1 - gamma_nu) in the baseline convention
+                proj = one + sign_fwd * gam[nu]
+                u = links[sites, nu]
+                w = tfac
+            else:  # psi(s - nu) through U_nu(s - nu)^dagger
+                proj = one - sign_fwd * gam[nu]
+                u = np.conj(np.swapaxes(links[nb, nu], -1, -2))
+                w = 1.0 / tfac
+            term = np.einsum("ab,scd,sbd->sac", proj, u, psi[nb])
+            out -= (kappa * w * bc)[:, None, None] * term
+    return out.reshape(len(sites), 12)
+
+
+def hw_sites(links, dims, mu, m_w, x, sites, convention="baseline"):
+    """(H_w(mu) x) = (gamma5 D_w(mu) x) at the listed sites (Sec. 2, Eq. Dov)."""
+    d = wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention)
+    return d * np.repeat(np.real(np.diag(gamma5())), 3)[None, :]
+
+
 def gamma5_diag(v):
     """Diagonal of gamma5 (x) 1_colour over all sites, length 12 V."""
     g5 = np.real(np.diag(gamma5()))
