@@ -1,7 +1,10 @@
 // K3: sgn(H_k) e_1 by Roberts' iteration S <- (S + S^-1)/2, S^0 = H_k
 // (Sec. 5.2, Eq. Roberts; used for H_k in Sec. 5.3 step v), in FP64 on the
-// device: a cluster of 8 thread blocks (8 SMs) per right-hand side for
-// k <= 320, one thread block per right-hand side above.
+// device: a thread-block cluster (one block per SM) per right-hand side
+// while the matrix fits the cluster's shared memory (k up to about 320), one
+// thread block per right-hand side above. The cluster size (4 to 8) is
+// chosen at launch so that the clusters of all right-hand sides are resident
+// in as few waves as possible.
 //
 // The inverse is an in-place Gauss-Jordan elimination with partial (row)
 // pivoting; the row interchanges are undone as column interchanges at the
@@ -12,6 +15,10 @@
 // imaginary axis makes S singular) ends with status OVS_ESIGN; no
 // convergence within 50 iterations gives OVS_NOT_CONVERGED.
 #include <cooperative_groups.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -205,9 +212,10 @@ __global__ void __launch_bounds__(NT) k_newton(const double2* __restrict__ H, lo
 }
 
 // ----------------------------------------------------------------------
-// Cluster form: one matrix per cluster of NCL CTAs (one per SM). CTA c holds
-// the column block [c*W, c*W + W) of the matrix being inverted in shared
-// memory (W = ceil(n/NCL)); the iterate S stays in global memory (each CTA
+// Cluster form: one matrix per cluster of ncl CTAs (one per SM; ncl is the
+// launch's cluster size). CTA c holds the column block [c*W, c*W + W) of the
+// matrix being inverted in shared memory (W = ceil(n/ncl)); the iterate S
+// stays in global memory (each CTA
 // touches only its own columns). Gauss-Jordan step p: the owner of column p
 // picks the pivot and publishes the pivot index and the (row-swapped)
 // column p in its shared memory, double-buffered by the parity of p; one
@@ -216,9 +224,8 @@ __global__ void __launch_bounds__(NT) k_newton(const double2* __restrict__ H, lo
 // eliminates. After the last step the row interchanges are undone as a
 // column permutation read from the owners' blocks while S <- (S + S^-1)/2 is
 // formed, and the norms of the change are summed over the cluster.
-constexpr int NCL = 8;
 constexpr int NTC = 512;
-constexpr int kClusterMaxN = 320;
+constexpr int kClusterSizes[] = {8, 7, 6, 5, 4};  // candidates, largest first
 
 __device__ __forceinline__ double cl_block_sum(double v, double* sh) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -232,7 +239,7 @@ __device__ __forceinline__ double cl_block_sum(double v, double* sh) {
     return s;
 }
 
-__global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
+__global__ void __launch_bounds__(NTC)
     k_newton_cluster(const double2* __restrict__ H, long long h_rhs_stride, int ldh, const int* __restrict__ k_used,
                      const double* __restrict__ beta, double2* __restrict__ coeff, long long coeff_stride,
                      double2* __restrict__ work, int kmax, int* __restrict__ iters, int* __restrict__ status,
@@ -245,11 +252,12 @@ __global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
     __shared__ double s_bv[NTC / 32];
     __shared__ int s_bi[NTC / 32];
     const int c = (int)cl.block_rank();
-    const int r = blockIdx.x / NCL;
+    const int ncl = (int)cl.num_blocks();
+    const int r = blockIdx.x / ncl;
     const int tid = threadIdx.x;
     if (active != nullptr && active[r] == 0) return;  // uniform over the cluster
     const int n = n_fixed > 0 ? n_fixed : k_used[r];
-    const int Wmax = (kmax + NCL - 1) / NCL;
+    const int Wmax = (kmax + ncl - 1) / ncl;
     cd* T = reinterpret_cast<cd*>(smem_raw);          // [kmax][Wmax]
     cd* colp = T + (size_t)kmax * Wmax;              // [2][kmax] published pivot columns
     cd* colL = colp + 2 * (size_t)kmax;               // [kmax] local copy
@@ -264,7 +272,7 @@ __global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
         }
         return;  // uniform over the cluster: n is the same for all its CTAs
     }
-    const int W = (n + NCL - 1) / NCL;
+    const int W = (n + ncl - 1) / ncl;
     const int c0 = c * W;
     const int w = max(0, min(n, c0 + W) - c0);
     cd* S = reinterpret_cast<cd*>(work) + (size_t)r * 2 * kmax * kmax;  // row-major n x n
@@ -393,7 +401,7 @@ __global__ void __cluster_dims__(NCL, 1, 1) __launch_bounds__(NTC)
         if (tid == 0) { s_part[0] = d2; s_part[1] = s2; }
         cl.sync();  // partials visible; remote reads of T finished
         double D2 = 0.0, S2 = 0.0;
-        for (int q = 0; q < NCL; ++q) {
+        for (int q = 0; q < ncl; ++q) {
             const double* rp = cl.map_shared_rank(s_part, q);
             D2 += rp[0];
             S2 += rp[1];
@@ -465,27 +473,87 @@ cudaError_t launch_conv_check(const void* cnew, const void* cold, long long stri
     return cudaGetLastError();
 }
 
-static size_t cluster_smem(int kmax) {
-    const int Wmax = (kmax + NCL - 1) / NCL;
+static size_t cluster_smem(int kmax, int ncl) {
+    const int Wmax = (kmax + ncl - 1) / ncl;
     return ((size_t)kmax * Wmax + 3 * (size_t)kmax + Wmax) * sizeof(cd) + 2 * (size_t)kmax * sizeof(int);
+}
+
+constexpr size_t kClusterSmemMax = 220 * 1024;
+
+// Cluster size for nrhs matrices of order <= kmax: the candidate with the
+// fewest waves per SM of a cluster (waves / ncl, the FP64 work per SM being
+// proportional to 1/ncl), 0 if none fits. Clusters of one block per SM are
+// placed within a GPC, so how many are resident at once depends on the size
+// and is asked of the runtime (cached per size and shared-memory need).
+static int pick_cluster(int kmax, int nrhs) {
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, int> resident;
+    static bool attr = false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_newton_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kClusterSmemMax) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        attr = true;
+    }
+    int best = 0;
+    double best_cost = 0.0;
+    for (int ncl : kClusterSizes) {
+        const size_t need = cluster_smem(kmax, ncl);
+        if (need > kClusterSmemMax) continue;
+        auto key = std::make_pair(ncl, need);
+        auto it = resident.find(key);
+        if (it == resident.end()) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = ncl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(ncl);
+            cfg.blockDim = dim3(NTC);
+            cfg.dynamicSmemBytes = need;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k_newton_cluster, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                n = 0;
+            }
+            it = resident.emplace(key, n).first;
+        }
+        if (it->second < 1) continue;
+        const int waves = (nrhs + it->second - 1) / it->second;
+        const double cost = (double)waves / ncl;
+        if (best == 0 || cost < best_cost - 1e-12) {
+            best = ncl;
+            best_cost = cost;
+        }
+    }
+    return best;
 }
 
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
                           int* status, cudaStream_t st, const int* active, int n_fixed) {
-    const size_t need = cluster_smem(kmax);
-    if (kmax <= kClusterMaxN && need <= 220 * 1024) {
-        static size_t attr_set = 0;  // dynamic shared memory opted in so far
-        if (need > attr_set) {
-            const cudaError_t e = cudaFuncSetAttribute(k_newton_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)need);
-            if (e != cudaSuccess) return e;
-            attr_set = need;
-        }
-        k_newton_cluster<<<nrhs * NCL, NTC, need, st>>>(
-            (const double2*)H, h_rhs_stride, ldh, k_used, beta, (double2*)coeff, coeff_stride, (double2*)work, kmax,
-            iters, status, active, n_fixed);
-        return cudaGetLastError();
+    const int ncl = pick_cluster(kmax, nrhs);
+    if (ncl > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = ncl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(nrhs * ncl);
+        cfg.blockDim = dim3(NTC);
+        cfg.dynamicSmemBytes = cluster_smem(kmax, ncl);
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_newton_cluster, (const double2*)H, h_rhs_stride, ldh, k_used, beta,
+                                  (double2*)coeff, coeff_stride, (double2*)work, kmax, iters, status, active, n_fixed);
     }
     const size_t smem = (size_t)kmax * 2 * sizeof(cd) + (size_t)kmax * sizeof(int);
     static bool attr = false;
