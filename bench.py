@@ -365,6 +365,11 @@ def run_ours(args, w, world, rank, local):
                        "status": ovs.STATUS.get(status, status)},
         "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
     }
+    tuned = ovs.stencil_tuning(g, ovs.MIXED, w["nrhs"])
+    if tuned is not None:  # the autotuner's choice for the timed stencil launches
+        rt, sites, rb = tuned["shape"]
+        out["stencil_shape"] = {"rhs_per_thread": rt, "sites_per_block": sites, "rhs_tiles_per_block": rb,
+                                "candidates_ms": {f"{a}x{b}x{c}": round(t, 4) for (a, b, c), t in tuned["ms"].items()}}
     g.destroy()
     return out
 

@@ -224,6 +224,38 @@ int ovs_sign_apply_batched(int32_t n, const ovs_gauge_t* g, const void* const* x
 /* Reports of the last ovs_sign_apply on this handle (waits for its stream). */
 int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs);
 
+/* Launch shape of the stencil (K1). A shape is (rt, sites, rb): rt
+ * right-hand sides per thread (1 or 2: the thread loads each link once for
+ * them) and a thread block of `sites` sites times `rb` right-hand-side
+ * tiles (the warps of a block share the links of their sites through L1),
+ * at most 256 threads. The 18 candidates are, in this order:
+ *   (1,32,1) (1,32,2) (1,32,4) (1,32,8) (1,64,1) (1,64,2) (1,64,4)
+ *   (1,128,1) (1,128,2) (2,32,1) (2,32,2) (2,32,4) (2,32,8) (2,64,1)
+ *   (2,64,2) (2,64,4) (2,128,1) (2,128,2).
+ * The first stencil launch of a handle for a (prec, nrhs) pair, made outside
+ * stream capture, times the candidates on the caller's stream with CUDA
+ * events (one warm-up and up to three timed launches each, on that call's
+ * operands; this synchronises the stream once) and keeps the fastest for
+ * the handle. OVS_F64 times only the rt = 1 shapes (the FP64 stencil is
+ * bound by the FP64 units whatever the shape). ovs_sign_apply_batched tunes
+ * before it records its graphs. A launch inside a capture that finds no
+ * choice uses (1, 128, 1) without storing it. Every shape gives
+ * bit-identical results. The paper has no counterpart: this is a service
+ * of the library. */
+
+/* The shape chosen for (prec, nrhs) in shape[0..2] = (rt, sites, rb) and, if
+ * ms is not NULL, the mean time in ms of each of the 18 candidates in the
+ * order above (negative: not timed or not launchable; 0 for all: the shape
+ * was pinned by ovs_set_stencil_shape). OVS_ESTATE if no shape has been
+ * chosen for the pair yet; EINVAL on bad arguments. */
+int ovs_stencil_tuning(ovs_gauge_t g, int32_t prec, int32_t nrhs, int32_t* shape, float* ms);
+
+/* Pin the shape (rt, sites, rb) used for (prec, nrhs) instead of timing the
+ * candidates; rt = 0 forgets the choice, so the next launch tunes again.
+ * The handle's recorded batched applications are dropped. EINVAL if the
+ * shape is not one of the 18 candidates. */
+int ovs_set_stencil_shape(ovs_gauge_t g, int32_t prec, int32_t nrhs, int32_t rt, int32_t sites, int32_t rb);
+
 /* Tracing. Every kernel a handle launches is counted per class, together
  * with its algorithmic bytes (the bytes the operation must move at least:
  * each operand read once, each result written once). With timing on, every

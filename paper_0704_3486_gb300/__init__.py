@@ -28,7 +28,8 @@ EXPORTS = [
     "ovs_create_gauge", "ovs_create_gauge_from_links", "ovs_get_links", "ovs_set_mu", "ovs_matvec",
     "ovs_matvec_noalloc",
     "ovs_deflate_setup", "ovs_deflate_stats", "ovs_set_setup_budget", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
-    "ovs_sign_apply", "ovs_sign_apply_batched", "ovs_get_info", "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
+    "ovs_sign_apply", "ovs_sign_apply_batched", "ovs_get_info", "ovs_stencil_tuning", "ovs_set_stencil_shape",
+    "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
     "ovs_destroy",
 ]
 PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout"]
@@ -87,6 +88,8 @@ def load(path=None):
         "ovs_sign_apply_batched": ([i32, vp, vp, vp, vp, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp],
                                    i32),
         "ovs_get_info": ([vp, ctypes.POINTER(ApplyInfo), i32], i32),
+        "ovs_stencil_tuning": ([vp, i32, i32, p_i32, vp], i32),
+        "ovs_set_stencil_shape": ([vp, i32, i32, i32, i32, i32], i32),
         "ovs_profile_enable": ([vp, i32], i32),
         "ovs_profile_read": ([vp, vp, vp, vp], i32),
         "ovs_last_error": ([], ctypes.c_char_p),
@@ -299,6 +302,31 @@ def get_info(g, nrhs):
     info = (ApplyInfo * nrhs)()
     st = _check(load().ovs_get_info(g.handle, info, int(nrhs)))
     return st, [i.as_dict() for i in info]
+
+
+STENCIL_SHAPES = [(1, 32, 1), (1, 32, 2), (1, 32, 4), (1, 32, 8), (1, 64, 1), (1, 64, 2), (1, 64, 4), (1, 128, 1),
+                  (1, 128, 2), (2, 32, 1), (2, 32, 2), (2, 32, 4), (2, 32, 8), (2, 64, 1), (2, 64, 2), (2, 64, 4),
+                  (2, 128, 1), (2, 128, 2)]
+
+
+def stencil_tuning(g, prec, nrhs):
+    """The stencil shape chosen for (prec, nrhs): {'shape': (rt, sites, rb),
+    'ms': {shape: mean ms of that candidate (negative: not timed)}}; None if
+    no shape has been chosen yet."""
+    import numpy as np
+    shape = (ctypes.c_int32 * 3)()
+    ms = np.zeros(len(STENCIL_SHAPES), dtype=np.float32)
+    st = load().ovs_stencil_tuning(g.handle, int(prec), int(nrhs), shape, _ptr(ms))
+    if st == -4:  # OVS_ESTATE: not chosen yet
+        return None
+    _check(st)
+    return {"shape": tuple(shape), "ms": {sh: float(v) for sh, v in zip(STENCIL_SHAPES, ms)}}
+
+
+def set_stencil_shape(g, prec, nrhs, shape):
+    """Pin the stencil shape (rt, sites, rb) for (prec, nrhs); None forgets it."""
+    rt, sites, rb = shape if shape is not None else (0, 0, 0)
+    _check(load().ovs_set_stencil_shape(g.handle, int(prec), int(nrhs), int(rt), int(sites), int(rb)))
 
 
 def profile_enable(g, timing=True):

@@ -138,6 +138,65 @@ static long long field_units(long long N, int tprec) { return tprec == PREC_F64 
 static int tprec_of(int prec) { return prec == OVS_MIXED ? PREC_F32 : PREC_F64; }
 static const void* links_for(const ovs_gauge_s* g, int tprec) { return tprec == PREC_F64 ? g->links64 : g->links32; }
 
+// Stencil autotuner (see ovs_stencil_tuning): every candidate shape timed
+// on st, one warm-up and up to 3 timed launches each, the fastest kept.
+StencilShape ovs::stencil_shape(ovs_gauge_s* g, int tp, int nrhs, const void* in, size_t in_stride, void* out,
+                                size_t out_stride, cudaStream_t st) {
+    const auto key = std::make_pair(tp, nrhs);
+    const auto it = g->tuned.find(key);
+    if (it != g->tuned.end()) return it->second.best;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (g->capturing || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return StencilShape{};
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return StencilShape{};
+    }
+    const void* L = links_for(g, tp);
+    ovs_gauge_s::Tuned t;
+    t.best = StencilShape{};
+    float best = -1.0f;
+    for (int i = 0; i < kNumStencilShapes; ++i) {
+        const StencilShape sh = kStencilShapes[i];
+        t.ms[i] = -1.0f;
+        if (tp == PREC_F64 && sh.rt != 1) continue;
+        auto run = [&]() {
+            return launch_wilson(tp, true, L, in, in_stride, out, out_stride, g->geom, nrhs, g->kappa, g->mu, nullptr,
+                                 st, sh);
+        };
+        // warm-up (timed: a launch over 1 ms is timed once more, else 3 times)
+        float ms = -1.0f;
+        cudaError_t e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        const int reps = (e == cudaSuccess && ms > 1.0f) ? 1 : 3;
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        t.ms[i] = ms / reps;
+        if (best < 0.0f || t.ms[i] < best) {
+            best = t.ms[i];
+            t.best = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->tuned[key] = t;
+    return t.best;
+}
+
 static void free_vec(VecWork& w) {
     dfree(w.xint);
     dfree(w.wvec);
@@ -375,16 +434,17 @@ int ovs_matvec(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, 
     const double bl = bytes_layout(N, tp, nrhs), bw = bytes_wilson(g->V, tp, nrhs);
     KL(OVS_PROF_LAYOUT, bl, launch_to_internal(tp, xd, N, w.xint, fb, (int)g->V, nrhs, st));
     const void* L = links_for(g, tp);
+    const StencilShape sh = stencil_shape(g, tp, nrhs, w.xint, fb, w.wvec, fb, st);
     if (op == OVS_OP_HW2) {
         KL(OVS_PROF_MATVEC, bw,
-           launch_wilson(tp, true, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
+           launch_wilson(tp, true, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st, sh));
         KL(OVS_PROF_MATVEC, bw,
-           launch_wilson(tp, true, L, w.wvec, fb, w.xint, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st));
+           launch_wilson(tp, true, L, w.wvec, fb, w.xint, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st, sh));
         KL(OVS_PROF_LAYOUT, bl, launch_to_canonical(tp, w.xint, fb, yd, N, (int)g->V, nrhs, st));
     } else {
         KL(OVS_PROF_MATVEC, bw,
            launch_wilson(tp, op == OVS_OP_HW, L, w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu, nullptr,
-                         st));
+                         st, sh));
         KL(OVS_PROF_LAYOUT, bl, launch_to_canonical(tp, w.wvec, fb, yd, N, (int)g->V, nrhs, st));
     }
     if (!ydev) {
@@ -732,11 +792,12 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
     // same sweep as the first pass of step j. u (in xint) is the first-pass
     // residual, x_ominus at the start; z = A u (in wvec).
     const double bw = bytes_wilson(g->V, tp, nrhs);
+    const StencilShape sh = stencil_shape(g, tp, nrhs, w.xint, fb, w.wvec, fb, st);
     for (int j = 0; j < k; ++j) {
         const int S = gdots_stride(2, j);
         KL(OVS_PROF_MATVEC, bw,
            launch_wilson(tp, true, links_for(g, tp), w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
-                         kw.active, st));
+                         kw.active, st, sh));
         const bool tma = (tp == PREC_F32) && tma_update_fits(j);
         const bool chunked = (tp == PREC_F32) && gdots_chunk_fits(j);
         const int dblk = chunked ? dslots : plan.nblk;
@@ -769,7 +830,7 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         if (tma)
             KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
                launch_arnoldi_update_tma(basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
-                                         w.xint, units, w.wvec, units, units, plan, nrhs, kw.active, kw.err, st));
+                                         w.xint, units, w.wvec, units, units, nrhs, g->num_sms, kw.active, kw.err, st));
         else
             KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
                launch_arnoldi_update(tp, basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
@@ -903,6 +964,8 @@ int ovs_sign_apply_batched(int32_t n, const ovs_gauge_t* gs, const void* const* 
         ovs_gauge_s* g = gs[i];
         if ((rc = ensure_vec(g, nrhs[i], tp)) < 0) break;
         if ((rc = ensure_kry(g, nrhs[i], opts->k_max, tp)) < 0) break;
+        // choose the stencil shape now: the recorded application cannot time it
+        stencil_shape(g, tp, nrhs[i], g->vw.xint, field_bytes(g->N, tp), g->vw.wvec, field_bytes(g->N, tp), st);
         if (!g->istream) e = cudaStreamCreateWithFlags(&g->istream, cudaStreamNonBlocking);
         if (e == cudaSuccess && !g->ev_join) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) break;
@@ -978,6 +1041,44 @@ int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
         else if (stt[r] == OVS_NOT_CONVERGED && worst == OVS_OK) worst = OVS_NOT_CONVERGED;
     }
     return worst;
+}
+
+int ovs_stencil_tuning(ovs_gauge_t g, int32_t prec, int32_t nrhs, int32_t* shape, float* ms) {
+    if (!g || !shape) return fail(OVS_EINVAL, "NULL argument");
+    if (prec != OVS_F64 && prec != OVS_MIXED) return fail(OVS_EINVAL, "bad prec");
+    if (nrhs < 1) return fail(OVS_EINVAL, "nrhs < 1");
+    const auto it = g->tuned.find(std::make_pair(tprec_of(prec), (int)nrhs));
+    if (it == g->tuned.end()) return fail(OVS_ESTATE, "no stencil shape chosen yet for this (prec, nrhs)");
+    shape[0] = it->second.best.rt;
+    shape[1] = it->second.best.sites;
+    shape[2] = it->second.best.rb;
+    if (ms)
+        for (int i = 0; i < kNumStencilShapes; ++i) ms[i] = it->second.ms[i];
+    return OVS_OK;
+}
+
+int ovs_set_stencil_shape(ovs_gauge_t g, int32_t prec, int32_t nrhs, int32_t rt, int32_t sites, int32_t rb) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (prec != OVS_F64 && prec != OVS_MIXED) return fail(OVS_EINVAL, "bad prec");
+    if (nrhs < 1) return fail(OVS_EINVAL, "nrhs < 1");
+    const auto key = std::make_pair(tprec_of(prec), (int)nrhs);
+    if (rt == 0) {
+        drop_graphs(g);
+        g->tuned.erase(key);
+        return OVS_OK;
+    }
+    for (int i = 0; i < kNumStencilShapes; ++i) {
+        const StencilShape& c = kStencilShapes[i];
+        if (c.rt == rt && c.sites == sites && c.rb == rb) {
+            drop_graphs(g);
+            ovs_gauge_s::Tuned t;
+            t.best = c;
+            for (int q = 0; q < kNumStencilShapes; ++q) t.ms[q] = 0.0f;
+            g->tuned[key] = t;
+            return OVS_OK;
+        }
+    }
+    return fail(OVS_EINVAL, "not one of the stencil shapes (see ovs_stencil_tuning)");
 }
 
 int ovs_profile_enable(ovs_gauge_t g, int32_t timing) {

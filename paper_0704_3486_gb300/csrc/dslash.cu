@@ -1,7 +1,12 @@
 // K1: the Wilson-Dirac stencil at chemical potential, H_w(mu) = gamma5 D_w(mu)
 // (Sec. 2, Eqs. Dov and Dw), and K7: field layout conversions.
 //
-// One thread per (site, right-hand side). Each of the eight hops projects
+// A thread block is a tile of sites (threadIdx.x) times a tile of
+// right-hand sides (threadIdx.y): the warps of one block work on the same
+// sites for different right-hand sides, so a link reaches shared L1 once per
+// block and not once per right-hand side. A thread may in addition take RT
+// right-hand sides (RT = 1 or 2), loading each link once for them. Each of
+// the eight hops projects
 // the neighbour's 4-spinor onto the rank-2 subspace of (1 -/+ gamma_nu)
 // (a 2 x 3 half spinor), multiplies the two colour vectors by U (forward)
 // or U^+ (backward), scales by kappa-independent factors (e^{+/-mu} on
@@ -68,13 +73,20 @@ template <> struct Field<float> {
         for (int q = 0; q < 6; ++q)
             d[(size_t)q * V + s] = make_float4(p[2 * q].re, p[2 * q].im, p[2 * q + 1].re, p[2 * q + 1].im);
     }
+    // complex64 links: per direction four float4 planes holding the entries
+    // (0,1) (2,3) (4,5) (6,7) of U (row-major 3x3), at float4 plane 4 nu + q;
+    // the ninth entry of every direction in float2 planes after those 16
+    // planes (float2 plane 32 + nu). Five loads per link instead of nine.
     __device__ __forceinline__ static void link(const void* u, int V, int nu, int s, cf (&m)[9]) {
-        const float2* d = static_cast<const float2*>(u) + (size_t)nu * 9 * V;
+        const float4* d = static_cast<const float4*>(u) + (size_t)nu * 4 * V;
 #pragma unroll
-        for (int e = 0; e < 9; ++e) {
-            float2 v = __ldg(d + (size_t)e * V + s);
-            m[e] = {v.x, v.y};
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = __ldg(d + (size_t)q * V + s);
+            m[2 * q] = {v.x, v.y};
+            m[2 * q + 1] = {v.z, v.w};
         }
+        const float2 w = __ldg(static_cast<const float2*>(u) + (size_t)(32 + nu) * V + s);
+        m[8] = {w.x, w.y};
     }
 };
 
@@ -142,24 +154,47 @@ __device__ __forceinline__ void hop_bwd(const cplx<R> (&p)[12], const cplx<R> (&
     }
 }
 
-template <int NU, typename R>
-__device__ __forceinline__ void both_hops(const void* links, const void* in, const Geom& g, int s, int coord,
-                                          R efwd, R ebwd, cplx<R> (&acc)[12]) {
+// Operands of one hop: the link and the neighbour spinors of the tile.
+template <typename R, int RT> struct HopData {
+    cplx<R> U[9];
+    cplx<R> p[RT][12];
+    R fac;
+};
+
+// Load the operands of the forward (FWD) or backward hop in direction NU:
+// U_NU(s) and psi(s + NU), or U_NU(s - NU) and psi(s - NU); the factor is
+// e^{+mu} / e^{-mu} on temporal hops (efwd / ebwd) and -1 on hops that
+// wrap in time (antiperiodic).
+template <int NU, bool FWD, typename R, int RT>
+__device__ __forceinline__ void hop_load(const void* links, const char* in, size_t in_stride, int r0,
+                                         const bool (&live)[RT], const Geom& g, int s, int coord, R efwd, R ebwd,
+                                         HopData<R, RT>& d) {
     const int L = g.L[NU], st = g.stride[NU];
-    const int sf = (coord == L - 1) ? s - (L - 1) * st : s + st;
-    const int sb = (coord == 0) ? s + (L - 1) * st : s - st;
-    R ff = efwd, fb = ebwd;
-    if (NU == 3) {
-        if (coord == L - 1) ff = -ff;  // antiperiodic in time
-        if (coord == 0) fb = -fb;
+    int sn;
+    if (FWD) {
+        sn = (coord == L - 1) ? s - (L - 1) * st : s + st;
+        d.fac = (NU == 3 && coord == L - 1) ? -efwd : efwd;
+        Field<R>::link(links, g.V, NU, s, d.U);
+    } else {
+        sn = (coord == 0) ? s + (L - 1) * st : s - st;
+        d.fac = (NU == 3 && coord == 0) ? -ebwd : ebwd;
+        Field<R>::link(links, g.V, NU, sn, d.U);
     }
-    cplx<R> U[9], p[12];
-    Field<R>::link(links, g.V, NU, s, U);
-    Field<R>::load(in, g.V, sf, p);
-    hop_fwd<NU>(p, U, ff, acc);
-    Field<R>::link(links, g.V, NU, sb, U);
-    Field<R>::load(in, g.V, sb, p);
-    hop_bwd<NU>(p, U, fb, acc);
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+        if (live[i]) Field<R>::load(in + (size_t)(r0 + i) * in_stride, g.V, sn, d.p[i]);
+}
+
+template <int NU, bool FWD, typename R, int RT>
+__device__ __forceinline__ void hop_apply(const HopData<R, RT>& d, const bool (&live)[RT], cplx<R> (&acc)[RT][12]) {
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+        if (!live[i]) continue;
+        if (FWD)
+            hop_fwd<NU>(d.p[i], d.U, d.fac, acc[i]);
+        else
+            hop_bwd<NU>(d.p[i], d.U, d.fac, acc[i]);
+    }
 }
 
 // Optional epilogue of the stencil: out = ah * (stencil result) + bx * X + by * Y
@@ -174,51 +209,98 @@ struct Axpy {
     double ah;
 };
 
-// out_r = [gamma5] (in_r - kappa * hops(in_r)) for r = blockIdx.y.
-// in/out strides are in bytes between right-hand sides.
-// Grid: x = right-hand side (fastest), y = tile of 128 sites, so the blocks
-// of all right-hand sides that share a tile of links run back to back and
-// read the links from L2 rather than once per right-hand side from DRAM.
-template <typename R, bool G5, bool AX = false>
-__global__ void __launch_bounds__(128) k_wilson(const void* __restrict__ links, const char* __restrict__ in,
+// out_r = [gamma5] (in_r - kappa * hops(in_r)) for the right-hand sides r
+// of the thread. in/out strides are in bytes between right-hand sides.
+// Blocks are numbered with the right-hand-side tile fastest, so the blocks
+// of all tiles that share a tile of sites (and of links) run back to back.
+template <typename R, bool G5, int RT, bool AX = false>
+__global__ void __launch_bounds__(256) k_wilson(const void* __restrict__ links, const char* __restrict__ in,
                                                 char* out, size_t in_stride, size_t out_stride, Geom g,
-                                                R kappa, R emu, R emmu, const int* __restrict__ active,
-                                                Axpy ax = Axpy{}) {
-    const int s = blockIdx.y * blockDim.x + threadIdx.x;
-    const int r = blockIdx.x;
-    if (s >= g.V) return;
-    if (active != nullptr && active[r] == 0) return;
-    const void* inr = in + r * in_stride;
-    void* outr = out + r * out_stride;
+                                                R kappa, R emu, R emmu, int nrhs, int ntiles,
+                                                const int* __restrict__ active, Axpy ax = Axpy{}) {
+    const int tile = blockIdx.x % ntiles;
+    const int s = (blockIdx.x / ntiles) * blockDim.x + threadIdx.x;
+    const int r0 = (tile * blockDim.y + threadIdx.y) * RT;
+    if (s >= g.V || r0 >= nrhs) return;
+    bool live[RT];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+        live[i] = (r0 + i < nrhs) && (active == nullptr || active[r0 + i] != 0);
+        any = any || live[i];
+    }
+    if (!any) return;
     int c = s;
     const int x = c % g.L[0]; c /= g.L[0];
     const int y = c % g.L[1]; c /= g.L[1];
     const int z = c % g.L[2];
     const int t = c / g.L[2];
-    cplx<R> acc[12];
+    cplx<R> acc[RT][12];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) acc[q] = {R(0), R(0)};
-    both_hops<0, R>(links, inr, g, s, x, R(1), R(1), acc);
-    both_hops<1, R>(links, inr, g, s, y, R(1), R(1), acc);
-    both_hops<2, R>(links, inr, g, s, z, R(1), R(1), acc);
-    both_hops<3, R>(links, inr, g, s, t, emu, emmu, acc);
-    cplx<R> p[12];
-    Field<R>::load(inr, g.V, s, p);
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
-        cplx<R> v = p[q] - acc[q] * kappa;
-        if (G5 && q >= 6) v = -v;
-        p[q] = v;
+        for (int q = 0; q < 12; ++q) acc[i][q] = {R(0), R(0)};
+    // the eight hops in a two-deep pipeline (RT = 1): the operands of the next
+    // hop are loaded before the current one is computed
+    HopData<R, RT> A, B;
+    const R one = R(1);
+    if (RT > 1) {  // registers of two RT-tiles in flight would spill: one hop at a time
+        hop_load<0, true>(links, in, in_stride, r0, live, g, s, x, one, one, A);
+        hop_apply<0, true>(A, live, acc);
+        hop_load<0, false>(links, in, in_stride, r0, live, g, s, x, one, one, A);
+        hop_apply<0, false>(A, live, acc);
+        hop_load<1, true>(links, in, in_stride, r0, live, g, s, y, one, one, A);
+        hop_apply<1, true>(A, live, acc);
+        hop_load<1, false>(links, in, in_stride, r0, live, g, s, y, one, one, A);
+        hop_apply<1, false>(A, live, acc);
+        hop_load<2, true>(links, in, in_stride, r0, live, g, s, z, one, one, A);
+        hop_apply<2, true>(A, live, acc);
+        hop_load<2, false>(links, in, in_stride, r0, live, g, s, z, one, one, A);
+        hop_apply<2, false>(A, live, acc);
+        hop_load<3, true>(links, in, in_stride, r0, live, g, s, t, emu, emmu, A);
+        hop_apply<3, true>(A, live, acc);
+        hop_load<3, false>(links, in, in_stride, r0, live, g, s, t, emu, emmu, A);
+        hop_apply<3, false>(A, live, acc);
+    } else {
+    hop_load<0, true>(links, in, in_stride, r0, live, g, s, x, one, one, A);
+    hop_load<0, false>(links, in, in_stride, r0, live, g, s, x, one, one, B);
+    hop_apply<0, true>(A, live, acc);
+    hop_load<1, true>(links, in, in_stride, r0, live, g, s, y, one, one, A);
+    hop_apply<0, false>(B, live, acc);
+    hop_load<1, false>(links, in, in_stride, r0, live, g, s, y, one, one, B);
+    hop_apply<1, true>(A, live, acc);
+    hop_load<2, true>(links, in, in_stride, r0, live, g, s, z, one, one, A);
+    hop_apply<1, false>(B, live, acc);
+    hop_load<2, false>(links, in, in_stride, r0, live, g, s, z, one, one, B);
+    hop_apply<2, true>(A, live, acc);
+    hop_load<3, true>(links, in, in_stride, r0, live, g, s, t, emu, emmu, A);
+    hop_apply<2, false>(B, live, acc);
+    hop_load<3, false>(links, in, in_stride, r0, live, g, s, t, emu, emmu, B);
+    hop_apply<3, true>(A, live, acc);
+    hop_apply<3, false>(B, live, acc);
     }
-    if (AX) {
-        cplx<R> xv[12], yv[12];
-        Field<R>::load(ax.X + r * ax.xs, g.V, s, xv);
-        Field<R>::load(ax.Y + r * ax.ys, g.V, s, yv);
-        const R ah = R(ax.ah), bx = R(ax.bx), by = R(ax.by);
 #pragma unroll
-        for (int q = 0; q < 12; ++q) p[q] = p[q] * ah + xv[q] * bx + yv[q] * by;
+    for (int i = 0; i < RT; ++i) {
+        if (!live[i]) continue;
+        const int r = r0 + i;
+        cplx<R> p[12];
+        Field<R>::load(in + (size_t)r * in_stride, g.V, s, p);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            cplx<R> v = p[q] - acc[i][q] * kappa;
+            if (G5 && q >= 6) v = -v;
+            p[q] = v;
+        }
+        if (AX) {
+            cplx<R> xv[12], yv[12];
+            Field<R>::load(ax.X + (size_t)r * ax.xs, g.V, s, xv);
+            Field<R>::load(ax.Y + (size_t)r * ax.ys, g.V, s, yv);
+            const R ah = R(ax.ah), bx = R(ax.bx), by = R(ax.by);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) p[q] = p[q] * ah + xv[q] * bx + yv[q] * by;
+        }
+        Field<R>::store(out + (size_t)r * out_stride, g.V, s, p);
     }
-    Field<R>::store(outr, g.V, s, p);
 }
 
 // Flat precision conversion of internal fields (the two layouts pair up).
@@ -294,7 +376,10 @@ __global__ void k_links_to_internal(const double2* __restrict__ canon, double2* 
         for (int e = 0; e < 9; ++e) {
             double2 v = canon[((size_t)s * 4 + nu) * 9 + e];
             u64[((size_t)nu * 9 + e) * V + s] = v;
-            if (u32 != nullptr) u32[((size_t)nu * 9 + e) * V + s] = make_float2(float(v.x), float(v.y));
+            if (u32 != nullptr) {  // complex64 layout of Field<float>::link
+                const size_t i = e < 8 ? ((size_t)(nu * 4 + e / 2) * V + s) * 2 + (e & 1) : (size_t)(32 + nu) * V + s;
+                u32[i] = make_float2(float(v.x), float(v.y));
+            }
         }
 }
 
@@ -310,28 +395,52 @@ __global__ void k_links_to_canonical(const double2* __restrict__ u64, double2* _
 // ------------------------------------------------------------- host launch
 static inline dim3 site_grid(int V, int nrhs, int threads) { return dim3((V + threads - 1) / threads, nrhs); }
 
-static inline dim3 rhs_site_grid(int V, int nrhs, int threads) { return dim3(nrhs, (V + threads - 1) / threads); }
+static bool valid_shape(const StencilShape& sh) {
+    for (int i = 0; i < kNumStencilShapes; ++i)
+        if (kStencilShapes[i].rt == sh.rt && kStencilShapes[i].sites == sh.sites && kStencilShapes[i].rb == sh.rb)
+            return true;
+    return false;
+}
+
+template <typename R, bool G5, bool AX>
+static void wilson_dispatch(const StencilShape& sh, unsigned blocks, int ntiles, cudaStream_t st, const void* links,
+                            const void* in, size_t in_stride, void* out, size_t out_stride, const Geom& g,
+                            double kappa, double emu, double emmu, int nrhs, const int* active, const Axpy& ax) {
+    const R k = (R)kappa, e1 = (R)emu, e2 = (R)emmu;
+    const char* i = (const char*)in;
+    char* o = (char*)out;
+    const dim3 block(sh.sites, sh.rb);
+    if (sh.rt == 1)
+        k_wilson<R, G5, 1, AX><<<blocks, block, 0, st>>>(links, i, o, in_stride, out_stride, g, k, e1, e2, nrhs, ntiles,
+                                                           active, ax);
+    else
+        k_wilson<R, G5, 2, AX><<<blocks, block, 0, st>>>(links, i, o, in_stride, out_stride, g, k, e1, e2, nrhs, ntiles,
+                                                           active, ax);
+}
 
 cudaError_t launch_wilson(int prec, bool gamma5, const void* links, const void* in, size_t in_stride, void* out,
                           size_t out_stride, const Geom& g, int nrhs, double kappa, double mu, const int* active,
-                          cudaStream_t st) {
-    const int T = 128;
-    dim3 grid = rhs_site_grid(g.V, nrhs, T);
+                          cudaStream_t st, StencilShape sh) {
+    if (!valid_shape(sh)) return cudaErrorInvalidValue;
+    const int ntiles = (nrhs + sh.rt * sh.rb - 1) / (sh.rt * sh.rb);
+    const long long blocks = (long long)ntiles * ((g.V + sh.sites - 1) / sh.sites);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const double emu = exp(mu), emmu = exp(-mu);
+    const Axpy ax{};
     if (prec == PREC_F64) {
         if (gamma5)
-            k_wilson<double, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
-                                                       kappa, emu, emmu, active);
+            wilson_dispatch<double, true, false>(sh, (unsigned)blocks, ntiles, st, links, in, in_stride, out,
+                                                 out_stride, g, kappa, emu, emmu, nrhs, active, ax);
         else
-            k_wilson<double, false><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
-                                                        kappa, emu, emmu, active);
+            wilson_dispatch<double, false, false>(sh, (unsigned)blocks, ntiles, st, links, in, in_stride, out,
+                                                  out_stride, g, kappa, emu, emmu, nrhs, active, ax);
     } else {
         if (gamma5)
-            k_wilson<float, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
-                                                      (float)kappa, (float)emu, (float)emmu, active);
+            wilson_dispatch<float, true, false>(sh, (unsigned)blocks, ntiles, st, links, in, in_stride, out,
+                                                out_stride, g, kappa, emu, emmu, nrhs, active, ax);
         else
-            k_wilson<float, false><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
-                                                       (float)kappa, (float)emu, (float)emmu, active);
+            wilson_dispatch<float, false, false>(sh, (unsigned)blocks, ntiles, st, links, in, in_stride, out,
+                                                 out_stride, g, kappa, emu, emmu, nrhs, active, ax);
     }
     return cudaGetLastError();
 }
@@ -339,17 +448,19 @@ cudaError_t launch_wilson(int prec, bool gamma5, const void* links, const void* 
 cudaError_t launch_wilson_axpy(int prec, const void* links, const void* in, size_t in_stride, void* out,
                                size_t out_stride, const void* X, size_t xs, double bx, const void* Y, size_t ys,
                                double by, double ah, const Geom& g, int nrhs, double kappa, double mu,
-                               cudaStream_t st) {
-    const int T = 128;
-    dim3 grid = rhs_site_grid(g.V, nrhs, T);
+                               cudaStream_t st, StencilShape sh) {
+    if (!valid_shape(sh)) return cudaErrorInvalidValue;
+    const int ntiles = (nrhs + sh.rt * sh.rb - 1) / (sh.rt * sh.rb);
+    const long long blocks = (long long)ntiles * ((g.V + sh.sites - 1) / sh.sites);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const double emu = exp(mu), emmu = exp(-mu);
-    Axpy ax{(const char*)X, xs, bx, (const char*)Y, ys, by, ah};
+    const Axpy ax{(const char*)X, xs, bx, (const char*)Y, ys, by, ah};
     if (prec == PREC_F64)
-        k_wilson<double, true, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
-                                                         kappa, emu, emmu, nullptr, ax);
+        wilson_dispatch<double, true, true>(sh, (unsigned)blocks, ntiles, st, links, in, in_stride, out, out_stride,
+                                            g, kappa, emu, emmu, nrhs, nullptr, ax);
     else
-        k_wilson<float, true, true><<<grid, T, 0, st>>>(links, (const char*)in, (char*)out, in_stride, out_stride, g,
-                                                        (float)kappa, (float)emu, (float)emmu, nullptr, ax);
+        wilson_dispatch<float, true, true>(sh, (unsigned)blocks, ntiles, st, links, in, in_stride, out, out_stride,
+                                           g, kappa, emu, emmu, nrhs, nullptr, ax);
     return cudaGetLastError();
 }
 

@@ -131,7 +131,8 @@ int apply_h(Ctx& c, int prec, const void* in, void* out, double mu) {
     ovs_gauge_s* g = c.g;
     const size_t fb = (size_t)c.N * (prec == PREC_F64 ? 16 : 8);
     const void* L = prec == PREC_F64 ? g->links64 : g->links32;
-    ECK(launch_wilson(prec, true, L, in, fb, out, fb, g->geom, c.p, g->kappa, mu, nullptr, c.st));
+    const StencilShape sh = stencil_shape(g, prec, c.p, in, fb, out, fb, c.st);
+    ECK(launch_wilson(prec, true, L, in, fb, out, fb, g->geom, c.p, g->kappa, mu, nullptr, c.st, sh));
     return OVS_OK;
 }
 
@@ -148,12 +149,13 @@ int cheb_filter(Ctx& c, int prec, void* bufs[3], int deg, double cc, double e, d
     void* prev = bufs[0];
     void* cur = bufs[1];
     void* tmp = bufs[2];
+    const StencilShape sh = stencil_shape(g, prec, c.p, prev, fb, tmp, fb, c.st);
     // Y1 = (sigma1/e) (H^2 - c) Y0
     {
         int rc = apply_h(c, prec, prev, tmp, mu);
         if (rc) return rc;
         ECK(launch_wilson_axpy(prec, L, tmp, fb, cur, fb, prev, fb, -sigma1 * cc / e, prev, fb, 0.0, sigma1 / e,
-                               g->geom, c.p, g->kappa, mu, c.st));
+                               g->geom, c.p, g->kappa, mu, c.st, sh));
     }
     for (int k = 1; k < deg; ++k) {
         const double sn = 1.0 / (2.0 / sigma1 - sigma);
@@ -161,7 +163,7 @@ int cheb_filter(Ctx& c, int prec, void* bufs[3], int deg, double cc, double e, d
         if (rc) return rc;
         // Y_{k+1} = (2 sn/e)(H^2 - c) Y_k - sigma sn Y_{k-1}, written over Y_{k-1}
         ECK(launch_wilson_axpy(prec, L, tmp, fb, prev, fb, cur, fb, -2.0 * sn * cc / e, prev, fb, -sigma * sn,
-                               2.0 * sn / e, g->geom, c.p, g->kappa, mu, c.st));
+                               2.0 * sn / e, g->geom, c.p, g->kappa, mu, c.st, sh));
         std::swap(prev, cur);
         sigma = sn;
     }

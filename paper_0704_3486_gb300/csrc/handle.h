@@ -3,10 +3,13 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "../../include/ovsign.h"
 #include "common.cuh"
+#include "kernels.h"
 
 struct VecWork {  // per-right-hand-side vectors
     int nrhs = 0, prec = -1;
@@ -90,6 +93,12 @@ struct ovs_gauge_s {
     bool capturing = false;
     cudaStream_t istream = nullptr;
     cudaEvent_t ev_join = nullptr;
+    // stencil launch shapes chosen per (internal precision, nrhs)
+    struct Tuned {
+        ovs::StencilShape best;
+        float ms[ovs::kNumStencilShapes];
+    };
+    std::map<std::pair<int, int>, Tuned> tuned;
     // statistics of the last ovs_deflate_setup
     int setup_iters[2] = {0, 0};
     long long setup_matvecs = 0;
@@ -103,4 +112,8 @@ int lib_fail(int code, const char* msg);
 // Install R (right) and L (left) vectors given as device canonical
 // complex128 [m][N]; L is biorthonormalised against R.
 int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, const double* lambda);
+// Stencil shape for (tp, nrhs) on this handle: the cached choice, else (not
+// capturing) the fastest candidate timed on st with in -> out as operands.
+StencilShape stencil_shape(ovs_gauge_s* g, int tp, int nrhs, const void* in, size_t in_stride, void* out,
+                           size_t out_stride, cudaStream_t st);
 }  // namespace ovs

@@ -12,14 +12,27 @@ struct Geom;
 enum { PREC_F64 = 0, PREC_F32 = 1 };
 
 // ---- K1 / K7 (dslash.cu)
+// Shape of a stencil launch: `rt` right-hand sides per thread (1 or 2), a
+// block of `sites` sites (threadIdx.x) times `rb` right-hand-side tiles
+// (threadIdx.y). Every shape gives bit-identical results (each output entry
+// is summed by one thread in the same order).
+struct StencilShape {
+    int rt = 1;
+    int sites = 128;
+    int rb = 1;
+};
+constexpr int kNumStencilShapes = 18;
+constexpr StencilShape kStencilShapes[kNumStencilShapes] = {
+    {1, 32, 1}, {1, 32, 2}, {1, 32, 4}, {1, 32, 8}, {1, 64, 1}, {1, 64, 2}, {1, 64, 4}, {1, 128, 1}, {1, 128, 2},
+    {2, 32, 1}, {2, 32, 2}, {2, 32, 4}, {2, 32, 8}, {2, 64, 1}, {2, 64, 2}, {2, 64, 4}, {2, 128, 1}, {2, 128, 2}};
 cudaError_t launch_wilson(int prec, bool gamma5, const void* links, const void* in, size_t in_stride, void* out,
                           size_t out_stride, const Geom& g, int nrhs, double kappa, double mu, const int* active,
-                          cudaStream_t st);
+                          cudaStream_t st, StencilShape shape = StencilShape{});
 // out = ah * H_w in + bx * X + by * Y (fused Chebyshev-recurrence step)
 cudaError_t launch_wilson_axpy(int prec, const void* links, const void* in, size_t in_stride, void* out,
                                size_t out_stride, const void* X, size_t xs, double bx, const void* Y, size_t ys,
                                double by, double ah, const Geom& g, int nrhs, double kappa, double mu,
-                               cudaStream_t st);
+                               cudaStream_t st, StencilShape shape = StencilShape{});
 // flat complex128 <-> complex64 conversion of internal fields (to_prec = target)
 cudaError_t launch_convert(int to_prec, const void* in, void* out, long long ncplx, cudaStream_t st);
 // uniform (-1,1) complex entries from a hash of (seed, index)
@@ -95,7 +108,7 @@ cudaError_t launch_gdots2_chunk(const void* basis, long long basis_rhs_stride, l
 cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, long long vec_stride, int J,
                                       const void* red, long long red_stride, const double* inv_beta,
                                       const void* dcoef, void* u, long long u_rhs_stride, const void* z,
-                                      long long z_rhs_stride, long long nunits, const BlasPlan& plan, int nrhs,
+                                      long long z_rhs_stride, long long nunits, int nrhs, int num_sms,
                                       const int* active, int* err, cudaStream_t st);
 
 // c'_r,i = sgn(Re lambda_i) * c_r,i

@@ -1,20 +1,23 @@
-// TMA-pipelined update sweep of the complex64 Arnoldi basis (K2).
+// TMA-pipelined sweeps over the complex64 Arnoldi basis: the inner products
+// (K1 dots) and the update (K2) of the delayed-reorthogonalisation step.
 //
-// The update sweep of an Arnoldi step (see blas.cu) streams the whole basis
-// of every right-hand side. Here the basis tiles reach shared memory through
-// 1D bulk asynchronous copies (cp.async.bulk, completion counted in bytes on
-// an mbarrier): a stage holds 8 basis vectors x 512 16-byte units (64 KB),
-// and 3 stages are in flight per block, so ~128 KB of loads per SM stay
-// outstanding without occupying registers. Thread 0 issues the copies; all
-// 256 threads consume a stage from shared memory and release it with a
-// block barrier (which also agrees on the wait), after which its buffer is
-// refilled (after a proxy fence, since generic loads read it before the
-// asynchronous copy overwrites it). The two sums of each thread's units stay
-// in registers across the stages of a tile.
+// Both sweeps stream the whole basis of every right-hand side once per
+// Arnoldi step, so they are bound by HBM bandwidth. Both are persistent
+// (one block per SM) and warp-specialised: one producer lane moves basis
+// tiles into shared memory with 1D bulk asynchronous copies (cp.async.bulk,
+// completion counted in bytes on an mbarrier), 3 stages of 8 vectors x 512
+// 16-byte units (64 KB each, 192 KB in flight per SM), and 8 consumer warps
+// read them and hand each stage back through a second mbarrier. The
+// producer refills a stage as soon as all consumer warps have released it
+// (after a proxy fence, since generic loads read the buffer before the
+// asynchronous copy overwrites it), so the consumers never wait for the
+// copy issue and may run up to 3 stages apart.
 //
-// Every wait on a stage is bounded: if a copy does not complete the block
-// records OVS_ETIMEOUT in *err, waits (bounded) for the copies it still has
-// in flight, and returns.
+// Every wait is bounded. A consumer whose wait runs out records OVS_ETIMEOUT
+// in *err and raises a shared abort flag; the other waits then give up at
+// once, the consumers leave together at their next common barrier, and the
+// producer waits (bounded) for the copies it still has in flight before the
+// block exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,38 +72,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Stage sequence of one block: for each tile of its row chunk, the groups
-// of TG basis vectors.
-template <int U, int NS>
-struct Seq {
-    const float4* V;  // basis of this right-hand side
-    long long vec_stride, u0, u1;
-    int J, ngroups;
-    __device__ void issue(int idx, unsigned char* stages, uint64_t* full) const {
-        const int s = idx % NS;
-        const int t = idx / ngroups, g = idx - t * ngroups;
-        const long long base = u0 + (long long)t * U;
-        const int units = (int)min((long long)U, u1 - base);
-        const int nv = min(TG, J - g * TG);
-        const uint32_t bytes = (uint32_t)units * 16u;
-        unsigned char* dst = stages + (size_t)s * TG * U * 16;
-        mbar_expect_tx(&full[s], bytes * nv);
-        for (int v = 0; v < nv; ++v)
-            bulk_load(dst + (size_t)v * U * 16, V + (long long)(g * TG + v) * vec_stride + base, bytes, &full[s]);
-    }
-};
-
-// Abort path (all threads): record the timeout and wait (bounded) for the
-// copies still in flight, so that no copy lands after the block has left.
-template <int NS>
-__device__ void drain(int idx, int total, uint64_t* full, int* err) {
-    if (threadIdx.x == 0) {
-        atomicExch(err, OVS_ETIMEOUT_CODE);
-        for (int q = idx; q < min(idx + NS, total); ++q) mbar_wait_bounded(&full[q % NS], (uint32_t)((q / NS) & 1));
-    }
-    __syncthreads();
-}
 
 }  // namespace
 
@@ -421,89 +392,154 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 //   v_J = (u - sum_i V_i s_i) / beta -> basis slot J,
 //   u   <- (z - sum_i V_i t_i) / beta - v_J d
 // with s, t from red[r] (s at 0, t at J), 1/beta = inv_beta[r], d = dcoef[r].
-// The basis streams through the same staged pipeline; the two sums of each
-// thread's units stay in registers across the groups of a tile.
-__global__ void __launch_bounds__(TB, 1)
-    k_arnoldi_update_tma(float4* __restrict__ basis, long long basis_rhs_stride, long long vec_stride, int J,
-                         const double2* __restrict__ red, long long red_stride, const double* __restrict__ inv_beta,
-                         const double2* __restrict__ dcoef, float4* __restrict__ u, long long u_rhs_stride,
-                         const float4* __restrict__ z, long long z_rhs_stride, long long nunits, long long chunk,
-                         const int* __restrict__ active, int* __restrict__ err) {
+// Persistent and warp-specialised like k_gdots2_ws: the work items are the
+// tiles of TU = 512 units of every right-hand side, flattened as (r, tile)
+// and split into one contiguous range per block; a tile takes one stage per
+// group of 8 basis vectors. A consumer thread keeps the two sums of its 2
+// units in registers across the groups of a tile and loads its u and z for
+// the tile's epilogue before the first group, so that load is hidden behind
+// the basis stream. The FP32 copies of s and t are reloaded into shared
+// memory when the block moves on to the next right-hand side.
+__global__ void __launch_bounds__(DTHREADS, 1)
+    k_arnoldi_update_ws(float4* __restrict__ basis, long long basis_rhs_stride, long long vec_stride, int J,
+                        const double2* __restrict__ red, long long red_stride, const double* __restrict__ inv_beta,
+                        const double2* __restrict__ dcoef, float4* __restrict__ u, long long u_rhs_stride,
+                        const float4* __restrict__ z, long long z_rhs_stride, long long nunits, int nrhs,
+                        const int* __restrict__ active, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[TNS];
-    unsigned char* stages = smem;
+    __shared__ __align__(8) uint64_t empty[TNS];
+    __shared__ int abort_flag;
     cf* sc = reinterpret_cast<cf*>(smem + TNS * kStageBytes);  // s at [0, J), t at [J, 2J)
-    const int r = blockIdx.y, b = blockIdx.x;
-    if (active != nullptr && active[r] == 0) return;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < 2 * J; i += TB) {
-        const double2 c = red[r * red_stride + i];
-        sc[i] = {float(c.x), float(c.y)};
-    }
-    Seq<TU, TNS> q;
-    q.V = basis + r * basis_rhs_stride;
-    q.vec_stride = vec_stride;
-    q.u0 = (long long)b * chunk;
-    q.u1 = min(q.u0 + chunk, nunits);
-    q.J = J;
-    q.ngroups = (J + TG - 1) / TG;
-    const int ntiles = (int)((q.u1 - q.u0 + TU - 1) / TU);
-    const int total = ntiles * q.ngroups;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, q = blockIdx.x;
+    const long long tpr = (nunits + TU - 1) / TU;  // tiles per right-hand side
+    const long long T = tpr * nrhs;
+    const long long lo = range_lo(q, T, G), hi = range_lo(q + 1, T, G);
+    const int ngroups = (J + TG - 1) / TG;
+    volatile int* abort = &abort_flag;
     if (tid == 0) {
-        for (int s = 0; s < TNS; ++s) mbar_init(&full[s], 1);
+        for (int k = 0; k < TNS; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], TW);
+        }
+        abort_flag = 0;
         mbar_fence_init();
     }
     __syncthreads();
-    if (tid == 0)
-        for (int idx = 0; idx < min(TNS, total); ++idx) q.issue(idx, stages, full);
-    const float ib = float(inv_beta[r]);
-    const double2 dd = dcoef[r];
-    const cf d = {float(dd.x), float(dd.y)};
-    float4* vout = basis + r * basis_rhs_stride + (long long)J * vec_stride;
-    float4* ur = u + r * u_rhs_stride;
-    const float4* zr = z + r * z_rhs_stride;
-    cf a[TE][2], bb[TE][2];
-    for (int t = 0; t < ntiles; ++t) {
-        const long long base = q.u0 + (long long)t * TU;
-#pragma unroll
-        for (int e = 0; e < TE; ++e) a[e][0] = a[e][1] = bb[e][0] = bb[e][1] = {0.f, 0.f};
-        for (int g = 0; g < q.ngroups; ++g) {
-            const int idx = t * q.ngroups + g, s = idx % TNS;
-            const bool got = mbar_wait_bounded(&full[s], (uint32_t)((idx / TNS) & 1));
-            const float4* st4 = reinterpret_cast<const float4*>(stages + (size_t)s * kStageBytes);
-            const int nv = min(TG, J - g * TG);
-#pragma unroll
-            for (int gi = 0; gi < TG; ++gi) {
-                if (gi < nv) {
-                    const cf si = sc[g * TG + gi], ti = sc[J + g * TG + gi];
-#pragma unroll
-                    for (int e = 0; e < TE; ++e) {
-                        cf vc[2];
-                        Unit<float>::split(st4[gi * TU + tid + TB * e], vc);
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            cfma(a[e][c], vc[c], si);
-                            cfma(bb[e][c], vc[c], ti);
-                        }
+
+    if (warp == TW) {  // ---- producer warp: one lane issues every stage
+        if (lane != 0 || ngroups == 0) return;
+        int n = 0;  // stages issued
+        bool ok = true;
+        for (long long it = lo; it < hi && ok; ++it) {
+            const long long r = it / tpr, base = (it - r * tpr) * TU;
+            if (active != nullptr && active[r] == 0) continue;
+            const uint32_t bytes = (uint32_t)min((long long)TU, nunits - base) * 16u;
+            const float4* Vr = basis + r * basis_rhs_stride + base;
+            for (int g = 0; g < ngroups; ++g) {
+                const int s = n % TNS;
+                if (n >= TNS) {  // the consumers' release of this stage's previous use
+                    if (!mbar_wait_or_abort(&empty[s], (uint32_t)((n / TNS - 1) & 1), abort)) {
+                        ok = false;
+                        break;
                     }
+                    fence_proxy_async_smem();
                 }
-            }
-            if (!__syncthreads_and(got)) {  // wait agreement + release of stage s
-                drain<TNS>(idx, total, full, err);
-                return;
-            }
-            if (tid == 0 && idx + TNS < total) {
-                fence_proxy_async_smem();
-                q.issue(idx + TNS, stages, full);
+                const int nv = min(TG, J - g * TG);
+                unsigned char* dst = smem + (size_t)s * kStageBytes;
+                mbar_expect_tx(&full[s], bytes * nv);
+                for (int v = 0; v < nv; ++v)
+                    bulk_load(dst + (size_t)v * TU * 16, Vr + (long long)(g * TG + v) * vec_stride, bytes, &full[s]);
+                ++n;
             }
         }
+        for (int k = max(0, n - TNS); k < n && ok; ++k)
+            ok = mbar_wait_or_abort(&empty[k % TNS], (uint32_t)((k / TNS) & 1), abort);
+        if (!ok) {
+            atomicExch(err, OVS_ETIMEOUT_CODE);
+            abort_flag = 1;
+            for (int k = max(0, n - TNS); k < n; ++k) mbar_wait_bounded(&full[k % TNS], (uint32_t)((k / TNS) & 1));
+        }
+        return;
+    }
+
+    // ---- consumer warps
+    int n = 0;  // stages consumed
+    long long seg_r = -1;
+    bool bad = false;
+    float ib = 0.f;
+    cf d = {0.f, 0.f};
+    for (long long it = lo; it < hi; ++it) {
+        const long long r = it / tpr, base = (it - r * tpr) * TU;
+        if (active != nullptr && active[r] == 0) continue;
+        if (r != seg_r) {  // coefficients of the next right-hand side
+            if (consumers_sync_or(bad)) return;  // everyone is done with the old ones
+            for (int i = tid; i < 2 * J; i += TB) {
+                const double2 c = red[r * red_stride + i];
+                sc[i] = {float(c.x), float(c.y)};
+            }
+            if (consumers_sync_or(bad)) return;
+            ib = float(inv_beta[r]);
+            const double2 dd = dcoef[r];
+            d = {float(dd.x), float(dd.y)};
+            seg_r = r;
+        }
+        float4* ur = u + r * u_rhs_stride;
+        const float4* zr = z + r * z_rhs_stride;
+        float4 up[TE], zp[TE];
 #pragma unroll
         for (int e = 0; e < TE; ++e) {
             const long long p = base + tid + (long long)TB * e;
-            if (p >= q.u1) continue;
+            up[e] = p < nunits ? ur[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+            zp[e] = p < nunits ? __ldg(zr + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cf a[TE][2], bb[TE][2];
+#pragma unroll
+        for (int e = 0; e < TE; ++e) a[e][0] = a[e][1] = bb[e][0] = bb[e][1] = {0.f, 0.f};
+        for (int g = 0; g < ngroups; ++g) {
+            const int s = n % TNS;
+            const bool got = bad || mbar_wait_or_abort(&full[s], (uint32_t)((n / TNS) & 1), abort);
+            if (!__all_sync(0xffffffffu, got)) {  // keep `bad` uniform over the warp
+                if (lane == 0) {
+                    atomicExch(err, OVS_ETIMEOUT_CODE);
+                    abort_flag = 1;
+                }
+                bad = true;
+            }
+            if (!bad) {
+                const float4* st4 = reinterpret_cast<const float4*>(smem + (size_t)s * kStageBytes);
+                const int nv = min(TG, J - g * TG);
+#pragma unroll
+                for (int gi = 0; gi < TG; ++gi) {
+                    if (gi < nv) {
+                        const cf si = sc[g * TG + gi], ti = sc[J + g * TG + gi];
+#pragma unroll
+                        for (int e = 0; e < TE; ++e) {
+                            cf vc[2];
+                            Unit<float>::split(st4[gi * TU + tid + TB * e], vc);
+#pragma unroll
+                            for (int c = 0; c < 2; ++c) {
+                                cfma(a[e][c], vc[c], si);
+                                cfma(bb[e][c], vc[c], ti);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+            }
+            ++n;
+        }
+        if (bad) continue;
+        float4* vout = basis + r * basis_rhs_stride + (long long)J * vec_stride;
+#pragma unroll
+        for (int e = 0; e < TE; ++e) {
+            const long long p = base + tid + (long long)TB * e;
+            if (p >= nunits) continue;
             cf uc[2], zc[2], vo[2], un[2];
-            Unit<float>::split(ur[p], uc);
-            Unit<float>::split(__ldg(zr + p), zc);
+            Unit<float>::split(up[e], uc);
+            Unit<float>::split(zp[e], zc);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 vo[c] = (uc[c] - a[e][c]) * ib;
@@ -558,21 +594,22 @@ cudaError_t launch_gdots2_chunk(const void* basis, long long basis_rhs_stride, l
 cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, long long vec_stride, int J,
                                       const void* red, long long red_stride, const double* inv_beta,
                                       const void* dcoef, void* u, long long u_rhs_stride, const void* z,
-                                      long long z_rhs_stride, long long nunits, const BlasPlan& plan, int nrhs,
+                                      long long z_rhs_stride, long long nunits, int nrhs, int num_sms,
                                       const int* active, int* err, cudaStream_t st) {
     static size_t set = 0;
     const size_t smem = TNS * kStageBytes + (size_t)(2 * J + 1) * sizeof(cf);
     if (smem > set) {
         const cudaError_t e =
-            cudaFuncSetAttribute(k_arnoldi_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_arnoldi_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         set = smem;
     }
-    dim3 grid(plan.nblk, nrhs);
-    k_arnoldi_update_tma<<<grid, TB, smem, st>>>((float4*)basis, basis_rhs_stride, vec_stride, J,
-                                                 (const double2*)red, red_stride, inv_beta, (const double2*)dcoef,
-                                                 (float4*)u, u_rhs_stride, (const float4*)z, z_rhs_stride, nunits,
-                                                 plan.chunk, active, err);
+    const long long T = (nunits + TU - 1) / TU * nrhs;
+    const int G = (int)std::max<long long>(1, std::min<long long>(num_sms, T));
+    k_arnoldi_update_ws<<<G, DTHREADS, smem, st>>>((float4*)basis, basis_rhs_stride, vec_stride, J,
+                                                   (const double2*)red, red_stride, inv_beta, (const double2*)dcoef,
+                                                   (float4*)u, u_rhs_stride, (const float4*)z, z_rhs_stride, nunits,
+                                                   nrhs, active, err);
     return cudaGetLastError();
 }
 
