@@ -22,7 +22,7 @@ the full spectrum.
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from .arnoldi import arnoldi_sign
+from .arnoldi import arnoldi_sign, arnoldi_sign_adaptive
 from .signfun import eig_decomposition, sgn_re
 
 
@@ -57,6 +57,24 @@ def lr_sign_apply(matvec, x, r, l, lam, k, **newton_kw):
     y_kr, info = arnoldi_sign(matvec, x_om, k, **newton_kw)
     info["c"] = c
     return y_defl + y_kr, info
+
+
+def lr_sign_apply_adaptive(matvec, x, r, l, lam, k_max, every, tol, **newton_kw):
+    """LR deflation (Eq. fAxLRArn) whose Krylov part stops by the convergence
+    estimate of ``arnoldi_sign_adaptive`` (the batched form's per-vector stop,
+    not in the paper): the deflated part is exact, so the estimate is taken
+    on the Krylov coefficients of x_ominus. Returns (y, info) as
+    ``lr_sign_apply``, with info["k_used"] the step of the stop."""
+    x = np.asarray(x, dtype=np.complex128)
+    if r is None or r.shape[1] == 0:
+        y, info = arnoldi_sign_adaptive(matvec, x, k_max, every, tol, **newton_kw)
+        info["c"] = np.zeros(0, np.complex128)
+        return y, info
+    l_bi = biorthonormalise(r, l)
+    c, x_om = lr_split(x, r, l_bi)
+    y_kr, info = arnoldi_sign_adaptive(matvec, x_om, k_max, every, tol, **newton_kw)
+    info["c"] = c
+    return r @ (sgn_re(lam) * c) + y_kr, info
 
 
 def critical_pairs_dense(a, m, decomposition=None):

@@ -22,6 +22,7 @@ sharing code with this module.
 from .philox import philox4x32_10, philox_uniform52
 from .gauge import gauge_links, unit_links, pure_gauge_links, random_su3, link_count
 from .vectors import gaussian_vectors, ones_vector, plane_wave_vectors
+from .workloads import batched_instances, synthetic_deflation
 
 __all__ = [
     "philox4x32_10",
@@ -34,4 +35,6 @@ __all__ = [
     "gaussian_vectors",
     "ones_vector",
     "plane_wave_vectors",
+    "batched_instances",
+    "synthetic_deflation",
 ]

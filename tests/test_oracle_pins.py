@@ -367,3 +367,24 @@ def test_adaptive_stops_and_matches_fixed_k():
     # the estimate tracks the true change: the error vs the dense sign is small
     ref = signfun.sgn_apply_dense(h.toarray(), x)
     assert rel(y, ref) < 1e-2
+
+
+def test_lr_adaptive_stop_matches_fixed_k_and_exact():
+    """The deflated adaptive form equals the fixed-k form at the step where it
+    stops, stops earlier than the undeflated adaptive form, and its result
+    is within a small multiple of the stopping tolerance of the dense sgn."""
+    h, n = _small_problem()
+    hd = h.toarray()
+    dec = signfun.eig_decomposition(hd)
+    x = synth.gaussian_vectors(n, 1, 5)[0]
+    ref = signfun.sgn_apply_dense(hd, x, dec)
+    lam, r, l = deflation.critical_pairs_dense(hd, 20, dec)
+    mv = lambda q: h @ q
+    y, info = deflation.lr_sign_apply_adaptive(mv, x, r, l, lam, 300, 10, 1e-8)
+    assert info["k_used"] % 10 == 0 and info["est"] < 1e-8
+    y_fixed, _ = deflation.lr_sign_apply(mv, x, r, l, lam, info["k_used"])
+    assert rel(y, y_fixed) < 1e-13
+    _, info0 = deflation.lr_sign_apply_adaptive(mv, x, None, None, None, 300, 10, 1e-8)
+    assert info["k_used"] < info0["k_used"]
+    assert rel(y, ref) < 1e-6
+
