@@ -851,9 +851,14 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
        launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.coeff, kmax, kw.newton, (int)kmax, nrhs, kw.iters,
                      kw.status, st));
     // K4: y += V_k c (Sec. 5.3 step vi)
-    KL(OVS_PROF_UPDATE, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
-       launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
-                     w.yacc, N, units, plan, nrhs, nullptr, nullptr, st));
+    if (tp == PREC_F32 && recombine_tma_fits(k))
+        KL(OVS_PROF_UPDATE, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
+           launch_recombine_tma(basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N, units,
+                                nrhs, g->num_sms, nullptr, kw.err, st));
+    else
+        KL(OVS_PROF_UPDATE, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
+           launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
+                         w.yacc, N, units, plan, nrhs, nullptr, nullptr, st));
     KL(OVS_PROF_LAYOUT, bytes_layout(N, PREC_F64, nrhs), launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
     (void)f64;
     return OVS_OK;

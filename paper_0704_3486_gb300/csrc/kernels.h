@@ -105,6 +105,13 @@ cudaError_t launch_gdots2_chunk(const void* basis, long long basis_rhs_stride, l
                                 const void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
                                 long long nunits, int nrhs, int num_sms, int nslot, void* partial, const int* active,
                                 int* err, cudaStream_t st);
+// y += alpha * sum_{i < min(J, Jdev[r])} V_i c_i: complex64 basis, complex128
+// y (internal layout, updated in place, y_rhs_stride in complex128 entries)
+bool recombine_tma_fits(int J);
+cudaError_t launch_recombine_tma(const void* basis, long long basis_rhs_stride, long long vec_stride, int J,
+                                 const int* Jdev, const void* coef, long long coef_stride, double alpha, void* y,
+                                 long long y_rhs_stride, long long nunits, int nrhs, int num_sms, const int* active,
+                                 int* err, cudaStream_t st);
 cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, long long vec_stride, int J,
                                       const void* red, long long red_stride, const double* inv_beta,
                                       const void* dcoef, void* u, long long u_rhs_stride, const void* z,

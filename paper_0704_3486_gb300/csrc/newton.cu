@@ -242,7 +242,7 @@ __device__ __forceinline__ double cl_block_sum(double v, double* sh) {
 __global__ void __launch_bounds__(NTC)
     k_newton_cluster(const double2* __restrict__ H, long long h_rhs_stride, int ldh, const int* __restrict__ k_used,
                      const double* __restrict__ beta, double2* __restrict__ coeff, long long coeff_stride,
-                     double2* __restrict__ work, int kmax, int* __restrict__ iters, int* __restrict__ status,
+                     double2* __restrict__ work, int kmax, int kc, int* __restrict__ iters, int* __restrict__ status,
                      const int* __restrict__ active, int n_fixed) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ unsigned char smem_raw[];
@@ -257,13 +257,14 @@ __global__ void __launch_bounds__(NTC)
     const int tid = threadIdx.x;
     if (active != nullptr && active[r] == 0) return;  // uniform over the cluster
     const int n = n_fixed > 0 ? n_fixed : k_used[r];
-    const int Wmax = (kmax + ncl - 1) / ncl;
-    cd* T = reinterpret_cast<cd*>(smem_raw);          // [kmax][Wmax]
-    cd* colp = T + (size_t)kmax * Wmax;              // [2][kmax] published pivot columns
-    cd* colL = colp + 2 * (size_t)kmax;               // [kmax] local copy
-    cd* rowp = colL + kmax;                           // [Wmax]
-    int* perm = reinterpret_cast<int*>(rowp + Wmax);  // [kmax]
-    int* srcc = perm + kmax;                          // [kmax]
+    // shared-memory layout for matrices of order <= kc (kc <= kmax)
+    const int Wmax = (kc + ncl - 1) / ncl;
+    cd* T = reinterpret_cast<cd*>(smem_raw);          // [kc][Wmax]
+    cd* colp = T + (size_t)kc * Wmax;                 // [2][kc] published pivot columns
+    cd* colL = colp + 2 * (size_t)kc;                 // [kc] local copy
+    cd* rowp = colL + kc;                             // [Wmax]
+    int* perm = reinterpret_cast<int*>(rowp + Wmax);  // [kc]
+    int* srcc = perm + kc;                            // [kc]
     double2* cr = coeff + r * coeff_stride;
     if (n <= 0) {
         if (c == 0) {
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(NTC)
                 const int piv = s_piv[buf];
                 for (int i = tid; i < n; i += NTC) {
                     const int si = (i == p) ? piv : (i == piv ? p : i);
-                    colp[(size_t)buf * kmax + i] = T[(size_t)si * W + jl];
+                    colp[(size_t)buf * kc + i] = T[(size_t)si * W + jl];
                 }
             }
             cl.sync();
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(NTC)
                 ok = false;
                 break;
             }
-            const cd* rcol = cl.map_shared_rank(colp + (size_t)buf * kmax, owner);
+            const cd* rcol = cl.map_shared_rank(colp + (size_t)buf * kc, owner);
             for (int i = tid; i < n; i += NTC) colL[i] = rcol[i];
             if (tid == 0) perm[p] = piv;
             if (piv != p) {
@@ -538,7 +539,10 @@ static int pick_cluster(int kmax, int nrhs) {
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
                           int* status, cudaStream_t st, const int* active, int n_fixed) {
-    const int ncl = pick_cluster(kmax, nrhs);
+    // matrices of a known order (the convergence checks) need shared memory
+    // for that order only, so they can use the cluster form below kmax
+    const int kc = (n_fixed > 0 && n_fixed < kmax) ? n_fixed : kmax;
+    const int ncl = pick_cluster(kc, nrhs);
     if (ncl > 0) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
@@ -548,12 +552,13 @@ cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const 
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(nrhs * ncl);
         cfg.blockDim = dim3(NTC);
-        cfg.dynamicSmemBytes = cluster_smem(kmax, ncl);
+        cfg.dynamicSmemBytes = cluster_smem(kc, ncl);
         cfg.stream = st;
         cfg.attrs = at;
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k_newton_cluster, (const double2*)H, h_rhs_stride, ldh, k_used, beta,
-                                  (double2*)coeff, coeff_stride, (double2*)work, kmax, iters, status, active, n_fixed);
+                                  (double2*)coeff, coeff_stride, (double2*)work, kmax, kc, iters, status, active,
+                                  n_fixed);
     }
     const size_t smem = (size_t)kmax * 2 * sizeof(cd) + (size_t)kmax * sizeof(int);
     static bool attr = false;

@@ -551,6 +551,159 @@ __global__ void __launch_bounds__(DTHREADS, 1)
     }
 }
 
+// Recombination y += alpha * sum_{i < J_r} V_i c_i (Eqs. yproj3, fAxLRArn)
+// of a complex64 basis into a complex128 vector, J_r = min(J, Jdev[r]) (the
+// Krylov depth of right-hand side r). Persistent and warp-specialised like
+// k_arnoldi_update_ws: tiles of TU = 512 units of every right-hand side, one
+// stage per group of 8 basis vectors. A consumer thread sums each group in
+// FP32 (8 terms per entry) and adds the partial to its FP64 accumulators, so
+// the FP64 work is two additions per complex entry and group. y (complex128
+// internal layout: complex64 unit u <-> complex128 entries 2u, 2u+1) is read
+// and written once per tile; its load is issued before the first group.
+__global__ void __launch_bounds__(DTHREADS, 1)
+    k_recombine_ws(const float4* __restrict__ basis, long long basis_rhs_stride, long long vec_stride, int J,
+                   const int* __restrict__ Jdev, const double2* __restrict__ coef, long long coef_stride,
+                   double alpha, double2* __restrict__ y, long long y_rhs_stride, long long nunits, int nrhs,
+                   const int* __restrict__ active, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[TNS];
+    __shared__ __align__(8) uint64_t empty[TNS];
+    __shared__ int abort_flag;
+    cf* sc = reinterpret_cast<cf*>(smem + TNS * kStageBytes);  // alpha * c, FP32, [0, J)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, q = blockIdx.x;
+    const long long tpr = (nunits + TU - 1) / TU;
+    const long long T = tpr * nrhs;
+    const long long lo = range_lo(q, T, G), hi = range_lo(q + 1, T, G);
+    volatile int* abort = &abort_flag;
+    auto depth = [&](long long r) { return Jdev != nullptr ? min(J, Jdev[r]) : J; };
+    if (tid == 0) {
+        for (int k = 0; k < TNS; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], TW);
+        }
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == TW) {  // ---- producer warp: one lane issues every stage
+        if (lane != 0) return;
+        int n = 0;
+        bool ok = true;
+        for (long long it = lo; it < hi && ok; ++it) {
+            const long long r = it / tpr, base = (it - r * tpr) * TU;
+            if (active != nullptr && active[r] == 0) continue;
+            const int Jr = depth(r);
+            const int ngroups = (Jr + TG - 1) / TG;
+            const uint32_t bytes = (uint32_t)min((long long)TU, nunits - base) * 16u;
+            const float4* Vr = basis + r * basis_rhs_stride + base;
+            for (int g = 0; g < ngroups; ++g) {
+                const int s = n % TNS;
+                if (n >= TNS) {
+                    if (!mbar_wait_or_abort(&empty[s], (uint32_t)((n / TNS - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async_smem();
+                }
+                const int nv = min(TG, Jr - g * TG);
+                unsigned char* dst = smem + (size_t)s * kStageBytes;
+                mbar_expect_tx(&full[s], bytes * nv);
+                for (int v = 0; v < nv; ++v)
+                    bulk_load(dst + (size_t)v * TU * 16, Vr + (long long)(g * TG + v) * vec_stride, bytes, &full[s]);
+                ++n;
+            }
+        }
+        for (int k = max(0, n - TNS); k < n && ok; ++k)
+            ok = mbar_wait_or_abort(&empty[k % TNS], (uint32_t)((k / TNS) & 1), abort);
+        if (!ok) {
+            atomicExch(err, OVS_ETIMEOUT_CODE);
+            abort_flag = 1;
+            for (int k = max(0, n - TNS); k < n; ++k) mbar_wait_bounded(&full[k % TNS], (uint32_t)((k / TNS) & 1));
+        }
+        return;
+    }
+
+    // ---- consumer warps
+    int n = 0;
+    long long seg_r = -1;
+    int Jr = 0;
+    bool bad = false;
+    for (long long it = lo; it < hi; ++it) {
+        const long long r = it / tpr, base = (it - r * tpr) * TU;
+        if (active != nullptr && active[r] == 0) continue;
+        if (r != seg_r) {  // coefficients of the next right-hand side
+            if (consumers_sync_or(bad)) return;
+            Jr = depth(r);
+            for (int i = tid; i < Jr; i += TB) {
+                const double2 c = coef[r * coef_stride + i];
+                sc[i] = {float(alpha * c.x), float(alpha * c.y)};
+            }
+            if (consumers_sync_or(bad)) return;
+            seg_r = r;
+        }
+        const int ngroups = (Jr + TG - 1) / TG;
+        double2* yr = y + r * y_rhs_stride;
+        double2 yo[TE][2];
+#pragma unroll
+        for (int e = 0; e < TE; ++e) {
+            const long long p = base + tid + (long long)TB * e;
+            yo[e][0] = p < nunits ? yr[2 * p] : make_double2(0.0, 0.0);
+            yo[e][1] = p < nunits ? yr[2 * p + 1] : make_double2(0.0, 0.0);
+        }
+        for (int g = 0; g < ngroups; ++g) {
+            const int s = n % TNS;
+            const bool got = bad || mbar_wait_or_abort(&full[s], (uint32_t)((n / TNS) & 1), abort);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) {
+                    atomicExch(err, OVS_ETIMEOUT_CODE);
+                    abort_flag = 1;
+                }
+                bad = true;
+            }
+            if (!bad) {
+                const float4* st4 = reinterpret_cast<const float4*>(smem + (size_t)s * kStageBytes);
+                const int nv = min(TG, Jr - g * TG);
+                cf a[TE][2];
+#pragma unroll
+                for (int e = 0; e < TE; ++e) a[e][0] = a[e][1] = {0.f, 0.f};
+#pragma unroll
+                for (int gi = 0; gi < TG; ++gi) {
+                    if (gi < nv) {
+                        const cf ci = sc[g * TG + gi];
+#pragma unroll
+                        for (int e = 0; e < TE; ++e) {
+                            cf vc[2];
+                            Unit<float>::split(st4[gi * TU + tid + TB * e], vc);
+#pragma unroll
+                            for (int c = 0; c < 2; ++c) cfma(a[e][c], vc[c], ci);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+#pragma unroll
+                for (int e = 0; e < TE; ++e)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        yo[e][c].x += double(a[e][c].re);
+                        yo[e][c].y += double(a[e][c].im);
+                    }
+            }
+            ++n;
+        }
+        if (bad) continue;
+#pragma unroll
+        for (int e = 0; e < TE; ++e) {
+            const long long p = base + tid + (long long)TB * e;
+            if (p >= nunits) continue;
+            yr[2 * p] = yo[e][0];
+            yr[2 * p + 1] = yo[e][1];
+        }
+    }
+}
+
 bool tma_update_fits(int J) { return TNS * kStageBytes + (size_t)(2 * J + 1) * sizeof(cf) <= 220 * 1024; }
 
 static size_t gdots_chunk_smem(int J) { return DS * kDStage + (size_t)(2 * J + 2) * 16; }
@@ -610,6 +763,28 @@ cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, l
                                                    (const double2*)red, red_stride, inv_beta, (const double2*)dcoef,
                                                    (float4*)u, u_rhs_stride, (const float4*)z, z_rhs_stride, nunits,
                                                    nrhs, active, err);
+    return cudaGetLastError();
+}
+
+bool recombine_tma_fits(int J) { return TNS * kStageBytes + (size_t)std::max(J, 1) * sizeof(cf) <= 220 * 1024; }
+
+cudaError_t launch_recombine_tma(const void* basis, long long basis_rhs_stride, long long vec_stride, int J,
+                                 const int* Jdev, const void* coef, long long coef_stride, double alpha, void* y,
+                                 long long y_rhs_stride, long long nunits, int nrhs, int num_sms, const int* active,
+                                 int* err, cudaStream_t st) {
+    static size_t set = 0;
+    const size_t smem = TNS * kStageBytes + (size_t)std::max(J, 1) * sizeof(cf);
+    if (smem > set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_recombine_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    const long long T = (nunits + TU - 1) / TU * nrhs;
+    const int G = (int)std::max<long long>(1, std::min<long long>(num_sms, T));
+    k_recombine_ws<<<G, DTHREADS, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J, Jdev,
+                                              (const double2*)coef, coef_stride, alpha, (double2*)y, y_rhs_stride,
+                                              nunits, nrhs, active, err);
     return cudaGetLastError();
 }
 

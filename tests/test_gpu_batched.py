@@ -135,3 +135,63 @@ def test_batched_errors(gpu):
     with pytest.raises(gpu.OvsError, match="twice"):
         gpu.sign_apply_batched([g, g], [x, x], [x.clone(), x.clone()], 4, prec=gpu.F64)
     g.destroy()
+
+
+def test_batched_instance_recipe(gpu):
+    """The batched workload's recipe (sizes cycling 4^4/6^4/8^4, mu cycling,
+    uneven right-hand-side counts, 20 deflation vectors each, per-vector stop)
+    in one batched call: every instance equals its single-instance result bit
+    for bit; every right-hand side either met the tolerance or ran to the cap,
+    at uneven depths; the FP64 form stops at the oracle's step on the 4^4
+    instances and matches it to 1e-12, the mixed form to 1e-6. The deflation
+    vectors are seeded stand-ins, which do not speed up convergence as the
+    critical eigenvectors do, so the stop is at 1e-6 within k = 300 (the
+    recipe's 1e-8 within 600 assumes the real deflation basis)."""
+    specs = synth.batched_instances(6)
+    k_cap, every, tol, m = 300, 10, 1e-6, 20
+    inst = []
+    for i, sp in enumerate(specs):
+        dims = sp["dims"]
+        n = 12 * int(np.prod(dims))
+        links = synth.gauge_links(dims, sp["gauge_seed"], sp["eps"])
+        g = gpu.create_gauge_from_links(dims, links, gpu.MIXED)
+        gpu.set_mu(g, sp["mu"], MW)
+        R, L, lam = synth.synthetic_deflation(n, m, 500 + i)
+        gpu.deflate_load(g, R.T.copy(), L.T.copy(), lam)
+        x = synth.gaussian_vectors(n, sp["nrhs"], sp["source_seed"])
+        inst.append((sp, links, g, x, (R, L, lam)))
+    gs = [i[2] for i in inst]
+    xs = [torch.from_numpy(i[3]).cuda() for i in inst]
+    ys = [torch.empty_like(x) for x in xs]
+    for prec in (gpu.MIXED, gpu.F64):
+        st, info = gpu.sign_apply_batched(gs, xs, ys, k_cap, prec=prec, check_every=every, tol=tol)
+        off = 0
+        ks = []
+        for (sp, links, g, x, (R, L, lam)), xd, yd in zip(inst, xs, ys):
+            nr = sp["nrhs"]
+            mine = info[off:off + nr]
+            off += nr
+            y_single = torch.empty_like(xd)
+            gpu.sign_apply(g, xd, y_single, k_cap, prec=prec, check_every=every, tol=tol)
+            assert torch.equal(yd, y_single)
+            for r, inf in enumerate(mine):
+                ks.append(inf["k_used"])
+                if inf["status"] == 0:
+                    assert inf["est_err"] < tol and inf["k_used"] % every == 0
+                else:
+                    assert inf["status"] == 1 and inf["k_used"] == k_cap
+            if sp["dims"] != (4, 4, 4, 4):
+                continue
+            h = lattice.hw_operator(links, sp["dims"], sp["mu"], MW)
+            y = yd.cpu().numpy()
+            for r in range(min(nr, 4)):
+                ref, oinfo = deflation.lr_sign_apply_adaptive(lambda q: h @ q, x[r], R, L, lam, k_cap, every, tol)
+                if prec == gpu.F64:
+                    assert mine[r]["k_used"] == oinfo["k_used"]
+                    assert rel(y[r], ref) < 1e-12
+                else:
+                    ref_k, _ = deflation.lr_sign_apply(lambda q: h @ q, x[r], R, L, lam, mine[r]["k_used"])
+                    assert rel(y[r], ref_k) < 1e-6
+        assert len(set(ks)) > 1  # uneven Krylov depths within the batch
+    for g in gs:
+        g.destroy()
