@@ -265,12 +265,13 @@ int ovs_set_stencil_shape(ovs_gauge_t g, int32_t prec, int32_t nrhs, int32_t rt,
  * fills up. */
 enum {
     OVS_PROF_MATVEC = 0, /* K1: H_w / D_w stencil */
-    OVS_PROF_DOTS = 1,   /* K2: Gram-Schmidt inner products (also L^+ x) */
-    OVS_PROF_UPDATE = 2, /* K2/K4/K5: basis updates, recombination, projection */
+    OVS_PROF_DOTS = 1,   /* K2: Gram-Schmidt inner products of the Arnoldi steps */
+    OVS_PROF_UPDATE = 2, /* K2: basis updates of the Arnoldi steps */
     OVS_PROF_SMALL = 3,  /* reductions, Hessenberg column, norms, scaling */
     OVS_PROF_NEWTON = 4, /* K3: Roberts iteration on H_k */
     OVS_PROF_LAYOUT = 5, /* K7: canonical <-> internal layout */
-    OVS_PROF_NCLASS = 6
+    OVS_PROF_PROJ = 6,   /* K4/K5: deflation projection (L^+ x, x - R c, R sgn c), recombination V_k c */
+    OVS_PROF_NCLASS = 7
 };
 
 /* Reset the counters; timing != 0 turns event timing on, 0 turns it off. */

@@ -32,7 +32,7 @@ EXPORTS = [
     "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
     "ovs_destroy",
 ]
-PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout"]
+PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout", "proj"]
 
 
 class OvsError(RuntimeError):

@@ -766,17 +766,17 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         const void* Lb = tp == PREC_F64 ? g->L64 : g->L32;
         const void* Rb = tp == PREC_F64 ? g->R64 : g->R32;
         const int S = gdots_stride(1, m);
-        KL(OVS_PROF_DOTS, bytes_dots(N, tp, m, nrhs, true),
+        KL(OVS_PROF_PROJ, bytes_dots(N, tp, m, nrhs, true),
            launch_gdots(tp, 1, Lb, 0, units, m, w.xint, units, nullptr, 0, false, units, plan, nrhs, kw.partial,
                         nullptr, st));
         KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
            launch_reduce(kw.partial, plan.nblk, S, m, nrhs, kw.cdef, m, false, nullptr, st));
         KL(OVS_PROF_SMALL, 32.0 * m * nrhs, launch_sign_scale(kw.cdef, g->sgn, m, nrhs, kw.cdef2, st));
-        KL(OVS_PROF_UPDATE, bytes_update(N, tp, tp, m, nrhs, true, true),
+        KL(OVS_PROF_PROJ, bytes_update(N, tp, tp, m, nrhs, true, true),
            launch_update(tp, tp, Rb, 0, units, m, nullptr, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, plan, nrhs,
                          nullptr, nullptr, st));
         // y = R sgn(Lambda) c in complex128 from the FP64 copy of R
-        KL(OVS_PROF_UPDATE, bytes_update(N, PREC_F64, PREC_F64, m, nrhs, true, false),
+        KL(OVS_PROF_PROJ, bytes_update(N, PREC_F64, PREC_F64, m, nrhs, true, false),
            launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cdef2, m, 1.0, nullptr, 0, w.yacc, N, N,
                          plan64, nrhs, nullptr, nullptr, st));
     } else {
@@ -852,11 +852,11 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
                      kw.status, st));
     // K4: y += V_k c (Sec. 5.3 step vi)
     if (tp == PREC_F32 && recombine_tma_fits(k))
-        KL(OVS_PROF_UPDATE, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
+        KL(OVS_PROF_PROJ, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
            launch_recombine_tma(basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N, units,
                                 nrhs, g->num_sms, nullptr, kw.err, st));
     else
-        KL(OVS_PROF_UPDATE, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
+        KL(OVS_PROF_PROJ, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
            launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
                          w.yacc, N, units, plan, nrhs, nullptr, nullptr, st));
     KL(OVS_PROF_LAYOUT, bytes_layout(N, PREC_F64, nrhs), launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
