@@ -109,6 +109,12 @@ def barrier(world):
         dist.barrier()
 
 
+def job_value(nrhs_per_rank, steps, world, ms_max):
+    """Whole-job applications/s: the right-hand sides all ranks processed in
+    the timed steps over the slowest rank's time."""
+    return nrhs_per_rank * steps * world / (ms_max / 1e3)
+
+
 def max_over_ranks(value, world, device):
     if world == 1:
         return value
@@ -286,7 +292,7 @@ def run_ours(args, w, world, rank, local):
     ovs.profile_enable(g, timing=False)
     status, info = ovs.get_info(g, w["nrhs"])
     ms_max = max_over_ranks(ms_total, world, dev)
-    value = w["nrhs"] * args.steps * world / (ms_max / 1e3)
+    value = job_value(w["nrhs"], args.steps, world, ms_max)
 
     # plain FP64, one right-hand side, same (m, k): time it and check the
     # mixed result of that right-hand side against it
