@@ -772,13 +772,29 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
            launch_reduce(kw.partial, plan.nblk, S, m, nrhs, kw.cdef, m, false, nullptr, st));
         KL(OVS_PROF_SMALL, 32.0 * m * nrhs, launch_sign_scale(kw.cdef, g->sgn, m, nrhs, kw.cdef2, st));
-        KL(OVS_PROF_PROJ, bytes_update(N, tp, tp, m, nrhs, true, true),
-           launch_update(tp, tp, Rb, 0, units, m, nullptr, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, plan, nrhs,
-                         nullptr, nullptr, st));
-        // y = R sgn(Lambda) c in complex128 from the FP64 copy of R
-        KL(OVS_PROF_PROJ, bytes_update(N, PREC_F64, PREC_F64, m, nrhs, true, false),
-           launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cdef2, m, 1.0, nullptr, 0, w.yacc, N, N,
-                         plan64, nrhs, nullptr, nullptr, st));
+        if (tp == PREC_F32 && m <= 1536)
+            KL(OVS_PROF_PROJ, bytes_update(N, tp, tp, m, nrhs, true, true),
+               launch_shared_combine(PREC_F32, Rb, units, m, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, nrhs, st));
+        else
+            KL(OVS_PROF_PROJ, bytes_update(N, tp, tp, m, nrhs, true, true),
+               launch_update(tp, tp, Rb, 0, units, m, nullptr, kw.cdef, m, -1.0, w.xint, N, w.xint, N, units, plan,
+                             nrhs, nullptr, nullptr, st));
+        // y = R sgn(Lambda) c into the complex128 accumulator: from the FP64
+        // copy of R in the FP64 form; from the complex64 copy (FP32 products,
+        // FP64 sums over 16 terms) in the mixed form, whose FP64 units would
+        // otherwise bound it (4 DFMA per complex entry and vector)
+        if (tp == PREC_F64)
+            KL(OVS_PROF_PROJ, bytes_update(N, PREC_F64, PREC_F64, m, nrhs, true, false),
+               launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cdef2, m, 1.0, nullptr, 0, w.yacc, N, N,
+                             plan64, nrhs, nullptr, nullptr, st));
+        else if (m <= 1536)
+            KL(OVS_PROF_PROJ, bytes_update(N, PREC_F32, PREC_F64, m, nrhs, true, false),
+               launch_shared_combine(PREC_F64, g->R32, units, m, kw.cdef2, m, 1.0, nullptr, 0, w.yacc, N, units, nrhs,
+                                     st));
+        else
+            KL(OVS_PROF_PROJ, bytes_update(N, PREC_F32, PREC_F64, m, nrhs, true, false),
+               launch_update(PREC_F32, PREC_F64, g->R32, 0, units, m, nullptr, kw.cdef2, m, 1.0, nullptr, 0, w.yacc,
+                             N, units, plan, nrhs, nullptr, nullptr, st));
     } else {
         CK(cudaMemsetAsync(w.yacc, 0, f64 * nrhs, st));
     }

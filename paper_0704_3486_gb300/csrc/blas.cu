@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(BT, sizeof(R) == 4 ? 2 : 1) k_gdots(const type
     constexpr int PER = M / 32;
     extern __shared__ double2 sacc2[];  // [NWARP][S]
     double* sacc = reinterpret_cast<double*>(sacc2);
-    const int r = blockIdx.y, b = blockIdx.x;
+    const int r = blockIdx.x, b = blockIdx.y;
     if (active != nullptr && active[r] == 0) return;
     const int S = NW * J + 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(BT) k_arnoldi_update(typename Unit<R>::vec* __
     constexpr int NC = Unit<R>::ncplx;
     extern __shared__ double2 scf[];
     cplx<R>* sc = reinterpret_cast<cplx<R>*>(scf);  // s at [0, J), t at [J, 2J)
-    const int r = blockIdx.y, b = blockIdx.x;
+    const int r = blockIdx.x, b = blockIdx.y;
     if (active != nullptr && active[r] == 0) return;
     const int tid = threadIdx.x;
     for (int i = tid; i < 2 * J; i += BT) {
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(BT) k_update(const typename Unit<RV>::vec* __r
     extern __shared__ double2 scoef2[];
     cplx<RV>* scoef = reinterpret_cast<cplx<RV>*>(scoef2);  // alpha*c, converted once per block
     __shared__ double sred[NWARP];
-    const int r = blockIdx.y, b = blockIdx.x;
+    const int r = blockIdx.x, b = blockIdx.y;
     if (active != nullptr && active[r] == 0) return;
     int Jr = J;
     if (Jdev != nullptr) Jr = min(J, Jdev[r]);
@@ -602,7 +602,7 @@ cudaError_t launch_gdots(int prec, int nw, const void* basis, long long basis_rh
                          bool extras, long long nunits, const BlasPlan& plan, int nrhs, void* partial,
                          const int* active, cudaStream_t st) {
     set_smem_attrs();
-    dim3 grid(plan.nblk, nrhs);
+    dim3 grid(nrhs, plan.nblk);  // right-hand side fastest: a shared basis is re-read from L2
     const size_t smem = (size_t)NWARP * gdots_stride(nw, J) * sizeof(double2);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     const int ex = extras ? 1 : 0;
@@ -636,7 +636,7 @@ cudaError_t launch_arnoldi_update(int prec, void* basis, long long basis_rhs_str
                                   long long nunits, const BlasPlan& plan, int nrhs, const int* active,
                                   cudaStream_t st) {
     set_smem_attrs();
-    dim3 grid(plan.nblk, nrhs);
+    dim3 grid(nrhs, plan.nblk);  // right-hand side fastest: a shared basis is re-read from L2
     const size_t smem = (size_t)std::max(2 * J, 1) * sizeof(double2);
     if (prec == PREC_F64)
         k_arnoldi_update<double, 2><<<grid, BT, smem, st>>>((double2*)basis, basis_rhs_stride, vec_stride, J,
@@ -673,7 +673,7 @@ cudaError_t launch_update(int prec_v, int prec_out, const void* basis, long long
                           long long nunits_v, const BlasPlan& plan, int nrhs, double* norm_partial,
                           const int* active, cudaStream_t st) {
     set_smem_attrs();
-    dim3 grid(plan.nblk, nrhs);
+    dim3 grid(nrhs, plan.nblk);  // right-hand side fastest: a shared basis is re-read from L2
     size_t smem = (size_t)std::max(J, 1) * sizeof(double2);
     if (prec_v == PREC_F64 && prec_out == PREC_F64) {
         k_update<double, double, 2><<<grid, BT, smem, st>>>(
@@ -693,6 +693,144 @@ cudaError_t launch_update(int prec_v, int prec_out, const void* basis, long long
     } else {
         return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// Shared-basis combination for all right-hand sides (the deflation part of
+// Sec. 5.3: x - R c and R sgn(Lambda) c, with R the complex64 copy of the
+// deflation basis): out_r = [in_r] + alpha * sum_{i < m} R_i c_{r,i}.
+// A block takes a tile of BT*2 units and a group of SG right-hand sides;
+// blocks are numbered with the group fastest, so the SG-groups of a tile
+// run together and R is read from DRAM once and from L2 by the other
+// groups. The vector loop is unrolled by 4 (8 loads in flight per thread);
+// products are FP32, and for a complex128 output the FP32 partial sums are
+// added into FP64 accumulators every 16 vectors.
+constexpr int SG = 4;
+template <typename RO>
+__global__ void __launch_bounds__(BT) k_shared_combine(const float4* __restrict__ R, long long vec_stride, int m,
+                                                       const double2* __restrict__ coef, long long coef_stride,
+                                                       double alpha, const cplx<RO>* in, long long in_rhs_stride,
+                                                       cplx<RO>* out, long long out_rhs_stride, long long nunits,
+                                                       int nrhs, int ngroups) {
+    extern __shared__ double2 smc[];
+    cf* sc = reinterpret_cast<cf*>(smc);  // [SG][m] alpha * c
+    const int grp = blockIdx.x % ngroups;
+    const long long tile = blockIdx.x / ngroups;
+    const int r0 = grp * SG;
+    const int nr = min(SG, nrhs - r0);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < SG * m; i += BT) {
+        const int q = i / m, v = i - q * m;
+        const double2 c = q < nr ? coef[(long long)(r0 + q) * coef_stride + v] : make_double2(0.0, 0.0);
+        sc[i] = {float(alpha * c.x), float(alpha * c.y)};
+    }
+    __syncthreads();
+    long long u[2];
+    bool ok[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        u[e] = tile * (2 * BT) + tid + (long long)BT * e;
+        ok[e] = u[e] < nunits;
+    }
+    cplx<RO> o[SG][2][2];
+    cf acc[SG][2][2];
+#pragma unroll
+    for (int q = 0; q < SG; ++q)
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                o[q][e][c] = {RO(0), RO(0)};
+                acc[q][e][c] = {0.f, 0.f};
+            }
+    auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < SG; ++q)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    o[q][e][c].re += RO(acc[q][e][c].re);
+                    o[q][e][c].im += RO(acc[q][e][c].im);
+                    acc[q][e][c] = {0.f, 0.f};
+                }
+    };
+    int i = 0;
+    for (; i + 4 <= m; i += 4) {
+        float4 v[4][2];
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                v[d][e] = ok[e] ? __ldg(R + (long long)(i + d) * vec_stride + u[e]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                cf vc[2];
+                Unit<float>::split(v[d][e], vc);
+#pragma unroll
+                for (int q = 0; q < SG; ++q) {
+                    const cf cq = sc[q * m + i + d];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) cfma(acc[q][e][c], vc[c], cq);
+                }
+            }
+        if (sizeof(RO) > 4 && ((i + 4) & 15) == 0) flush();
+    }
+    for (; i < m; ++i) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float4 v = ok[e] ? __ldg(R + (long long)i * vec_stride + u[e]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            cf vc[2];
+            Unit<float>::split(v, vc);
+#pragma unroll
+            for (int q = 0; q < SG; ++q) {
+                const cf cq = sc[q * m + i];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) cfma(acc[q][e][c], vc[c], cq);
+            }
+        }
+    }
+    flush();
+#pragma unroll
+    for (int q = 0; q < SG; ++q) {
+        if (q >= nr) break;
+        const int r = r0 + q;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (!ok[e]) continue;
+            cplx<RO> res[2];
+            if (in != nullptr) OutIO<RO, 2>::load(in + (long long)r * in_rhs_stride, u[e], res);
+            else res[0] = res[1] = {RO(0), RO(0)};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                res[c].re += o[q][e][c].re;
+                res[c].im += o[q][e][c].im;
+            }
+            OutIO<RO, 2>::store(out + (long long)r * out_rhs_stride, u[e], res);
+        }
+    }
+}
+
+cudaError_t launch_shared_combine(int prec_out, const void* R, long long vec_stride, int m, const void* coef,
+                                  long long coef_stride, double alpha, const void* in, long long in_rhs_stride,
+                                  void* out, long long out_rhs_stride, long long nunits, int nrhs, cudaStream_t st) {
+    if (m < 1 || nrhs < 1) return cudaErrorInvalidValue;
+    const int ngroups = (nrhs + SG - 1) / SG;
+    const long long tiles = (nunits + 2 * BT - 1) / (2 * BT);
+    const long long blocks = tiles * ngroups;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)SG * m * sizeof(cf);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    if (prec_out == PREC_F64)
+        k_shared_combine<double><<<(unsigned)blocks, BT, smem, st>>>(
+            (const float4*)R, vec_stride, m, (const double2*)coef, coef_stride, alpha, (const cd*)in, in_rhs_stride,
+            (cd*)out, out_rhs_stride, nunits, nrhs, ngroups);
+    else
+        k_shared_combine<float><<<(unsigned)blocks, BT, smem, st>>>(
+            (const float4*)R, vec_stride, m, (const double2*)coef, coef_stride, alpha, (const cf*)in, in_rhs_stride,
+            (cf*)out, out_rhs_stride, nunits, nrhs, ngroups);
     return cudaGetLastError();
 }
 

@@ -75,6 +75,13 @@ cudaError_t launch_update(int prec_v, int prec_out, const void* basis, long long
                           long long nunits_v, const BlasPlan& plan, int nrhs, double* norm_partial,
                           const int* active, cudaStream_t st);
 
+// out_r = [in_r] + alpha * sum_{i < m} R_i c_{r,i} for a complex64 basis R
+// shared by all right-hand sides (m <= 1536); out complex128 (prec_out = F64,
+// strides in complex128 entries) or complex64 (F32, strides in complex64
+// entries); in may be nullptr or equal to out
+cudaError_t launch_shared_combine(int prec_out, const void* R, long long vec_stride, int m, const void* coef,
+                                  long long coef_stride, double alpha, const void* in, long long in_rhs_stride,
+                                  void* out, long long out_rhs_stride, long long nunits, int nrhs, cudaStream_t st);
 // sum partial[r][b][i] (row stride pstride) over b -> out[r*out_stride + i], i < J
 cudaError_t launch_reduce(const void* partial, int nblk, int pstride, int J, int nrhs, void* out,
                           long long out_stride, bool accumulate, const int* active, cudaStream_t st);
