@@ -54,6 +54,7 @@ __device__ __forceinline__ double blk_sum(double v, double* sh) {
 __device__ bool gauss_jordan(cd* A, int n, int* perm, cd* colp, cd* rowp, double* sval, int* sidx) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     __shared__ int s_ok;
+    __shared__ double2 s_inv;
     if (tid == 0) s_ok = 1;
     for (int p = 0; p < n; ++p) {
         // pivot: argmax_{i >= p} |A[i][p]|
@@ -77,7 +78,13 @@ __device__ bool gauss_jordan(cd* A, int n, int* perm, cd* colp, cd* rowp, double
             for (int q = 1; q < NT / 32; ++q)
                 if (sval[q] > b || (sval[q] == b && sidx[q] < ib)) { b = sval[q]; ib = sidx[q]; }
             perm[p] = ib;
-            if (!(b > 0.0) || !isfinite(b)) s_ok = 0;
+            if (!(b > 0.0) || !isfinite(b)) {
+                s_ok = 0;
+            } else {  // the pivot's inverse, once per block (A[ib][p] is A[p][p] after the swap)
+                const cd a = A[(size_t)ib * n + p];
+                const double den = a.re * a.re + a.im * a.im;
+                s_inv = make_double2(a.re / den, -a.im / den);
+            }
         }
         __syncthreads();
         if (!s_ok) return false;
@@ -90,9 +97,7 @@ __device__ bool gauss_jordan(cd* A, int n, int* perm, cd* colp, cd* rowp, double
             }
             __syncthreads();
         }
-        const cd a = A[(size_t)p * n + p];
-        const double den = a.re * a.re + a.im * a.im;
-        const cd inv = {a.re / den, -a.im / den};
+        const cd inv = {s_inv.x, s_inv.y};
         for (int i = tid; i < n; i += NT) {
             colp[i] = A[(size_t)i * n + p];
             rowp[i] = (i == p) ? inv : cmul(A[(size_t)p * n + i], inv);
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__(NTC)
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_piv[2], s_ok[2];
+    __shared__ double2 s_inv;
     __shared__ double s_part[2];
     __shared__ double s_red[NTC / 32];
     __shared__ double s_bv[NTC / 32];
@@ -276,6 +282,10 @@ __global__ void __launch_bounds__(NTC)
     const int W = (n + ncl - 1) / ncl;
     const int c0 = c * W;
     const int w = max(0, min(n, c0 + W) - c0);
+    // elimination mapping: a fixed column ej and every erows-th row from ei
+    // (threads beyond erows * W idle there)
+    const int erows = NTC / W;
+    const int ej = tid % W, ei = tid / W;
     cd* S = reinterpret_cast<cd*>(work) + (size_t)r * 2 * kmax * kmax;  // row-major n x n
     const double2* Hr = H + r * h_rhs_stride;
     for (int idx = tid; idx < n * w; idx += NTC) {
@@ -333,7 +343,12 @@ __global__ void __launch_bounds__(NTC)
             }
             const cd* rcol = cl.map_shared_rank(colp + (size_t)buf * kc, owner);
             for (int i = tid; i < n; i += NTC) colL[i] = rcol[i];
-            if (tid == 0) perm[p] = piv;
+            if (tid == 0) {  // the pivot's inverse, once per block
+                perm[p] = piv;
+                const cd a = rcol[p];
+                const double den = a.re * a.re + a.im * a.im;
+                s_inv = make_double2(a.re / den, -a.im / den);
+            }
             if (piv != p) {
                 for (int jj = tid; jj < w; jj += NTC) {
                     const cd t = T[(size_t)p * W + jj];
@@ -342,26 +357,27 @@ __global__ void __launch_bounds__(NTC)
                 }
             }
             __syncthreads();
-            const cd a = colL[p];
-            const double den = a.re * a.re + a.im * a.im;
-            const cd inv = {a.re / den, -a.im / den};
+            const cd inv = {s_inv.x, s_inv.y};
             for (int jj = tid; jj < w; jj += NTC)
                 rowp[jj] = (c0 + jj == p) ? inv : cmul(T[(size_t)p * W + jj], inv);
             __syncthreads();
-            for (int idx = tid; idx < n * w; idx += NTC) {
-                const int i = idx / w, jj = idx - i * w;
-                if (i == p) {
-                    T[(size_t)i * W + jj] = rowp[jj];
-                } else if (c0 + jj == p) {
-                    T[(size_t)i * W + jj] = -cmul(colL[i], inv);
-                } else {
-                    cd v = T[(size_t)i * W + jj];
-                    const cd f = colL[i], gg = rowp[jj];
-                    v.re = fma(-f.re, gg.re, v.re);
-                    v.re = fma(f.im, gg.im, v.re);
-                    v.im = fma(-f.re, gg.im, v.im);
-                    v.im = fma(-f.im, gg.re, v.im);
-                    T[(size_t)i * W + jj] = v;
+            if (ej < w && ei < erows) {  // this thread's column ej, rows ei, ei + erows, ...
+                const cd gg = rowp[ej];
+                const bool pcol = (c0 + ej == p);
+                for (int i = ei; i < n; i += erows) {
+                    if (i == p) {
+                        T[(size_t)i * W + ej] = gg;
+                    } else if (pcol) {
+                        T[(size_t)i * W + ej] = -cmul(colL[i], inv);
+                    } else {
+                        cd v = T[(size_t)i * W + ej];
+                        const cd f = colL[i];
+                        v.re = fma(-f.re, gg.re, v.re);
+                        v.re = fma(f.im, gg.im, v.re);
+                        v.im = fma(-f.re, gg.im, v.im);
+                        v.im = fma(-f.im, gg.re, v.im);
+                        T[(size_t)i * W + ej] = v;
+                    }
                 }
             }
             __syncthreads();
