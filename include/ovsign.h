@@ -186,7 +186,9 @@ typedef struct {
 typedef struct {
     int32_t k_used;       /* Krylov dimension used (< k_max after breakdown) */
     int32_t newton_iters; /* Roberts iterations on H_k */
-    int32_t status;       /* OVS_OK, OVS_NOT_CONVERGED or OVS_ESIGN */
+    int32_t status;       /* OVS_OK, OVS_NOT_CONVERGED, OVS_ESIGN, or OVS_EINVAL
+                             when the source of this right-hand side is not
+                             finite (the call then returns OVS_EINVAL) */
     int32_t reserved;
     double beta;          /* ||x_ominus||, the norm of the deflated source */
     double est_err;       /* last error estimate (check_every > 0), else 0 */
@@ -281,6 +283,16 @@ int ovs_profile_enable(ovs_gauge_t g, int32_t timing);
  * ms[c] device milliseconds (0 without timing), launches[c], bytes[c]
  * algorithmic bytes, for c < OVS_PROF_NCLASS. Waits for timed launches. */
 int ovs_profile_read(ovs_gauge_t g, double* ms, int64_t* launches, double* bytes);
+
+/* Self-check of the timeout path of the bounded device waits (the paper has
+ * no counterpart). Every wait of the library's kernels on a flag or an
+ * mbarrier is bounded: when it gives up, the kernel records OVS_ETIMEOUT in
+ * an error word, lets its copies in flight land, and returns, and the call
+ * reports OVS_ETIMEOUT. This launches one block whose wait can never
+ * complete (nothing arrives on its mbarrier) and waits for it on `stream`
+ * (about a second). Returns OVS_ETIMEOUT when the bound works, OVS_ECUDA
+ * otherwise. The context stays usable. */
+int ovs_check_wait_timeout(void* stream);
 
 /* Thread-local message of the last error (never NULL). */
 const char* ovs_last_error(void);

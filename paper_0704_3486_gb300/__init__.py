@@ -29,7 +29,7 @@ EXPORTS = [
     "ovs_matvec_noalloc",
     "ovs_deflate_setup", "ovs_deflate_stats", "ovs_set_setup_budget", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
     "ovs_sign_apply", "ovs_sign_apply_batched", "ovs_get_info", "ovs_stencil_tuning", "ovs_set_stencil_shape",
-    "ovs_profile_enable", "ovs_profile_read", "ovs_last_error", "ovs_version",
+    "ovs_profile_enable", "ovs_profile_read", "ovs_check_wait_timeout", "ovs_last_error", "ovs_version",
     "ovs_destroy",
 ]
 PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout", "proj"]
@@ -91,6 +91,7 @@ def load(path=None):
         "ovs_stencil_tuning": ([vp, i32, i32, p_i32, vp], i32),
         "ovs_set_stencil_shape": ([vp, i32, i32, i32, i32, i32], i32),
         "ovs_profile_enable": ([vp, i32], i32),
+        "ovs_check_wait_timeout": ([vp], i32),
         "ovs_profile_read": ([vp, vp, vp, vp], i32),
         "ovs_last_error": ([], ctypes.c_char_p),
         "ovs_version": ([], ctypes.c_char_p),
@@ -343,6 +344,12 @@ def profile_read(g):
     _check(load().ovs_profile_read(g.handle, _ptr(ms), _ptr(launches), _ptr(nbytes)))
     return {c: {"ms": float(ms[i]), "launches": int(launches[i]), "bytes": float(nbytes[i])}
             for i, c in enumerate(PROF_CLASSES)}
+
+
+def check_wait_timeout(stream=None):
+    """Run the bounded-wait self-check; returns the status (OVS_ETIMEOUT = -7
+    when the timeout path works)."""
+    return load().ovs_check_wait_timeout(_stream(stream))
 
 
 def version():

@@ -33,6 +33,10 @@ using namespace ovs;
 // --------------------------------------------------------------- errors
 static thread_local std::string g_err = "no error";
 
+// Record the message and return code. A failed runtime call (e.g. an
+// allocation beyond the device) leaves a non-sticky "last error" that the
+// next launch check would report again: it is cleared here, so the handle
+// stays usable after a reported failure. Sticky errors are not affected.
 static int fail(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -40,6 +44,7 @@ static int fail(int code, const char* fmt, ...) {
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
     g_err = buf;
+    if (code == OVS_ECUDA || code == OVS_ENOMEM) cudaGetLastError();
     return code;
 }
 
@@ -1046,8 +1051,12 @@ int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
         CK(cudaMemset(g->kw.err, 0, sizeof(int)));
         return fail(OVS_ETIMEOUT, "a bounded device wait gave up during the last sign application");
     }
-    int worst = OVS_OK;
+    int worst = OVS_OK, bad_rhs = -1;
     for (int r = 0; r < nrhs; ++r) {
+        if (!std::isfinite(beta[r])) {  // the (deflated) source had a NaN or an infinity
+            stt[r] = OVS_EINVAL;
+            if (bad_rhs < 0) bad_rhs = r;
+        }
         info[r].k_used = ku[r];
         info[r].newton_iters = it[r];
         info[r].status = stt[r];
@@ -1061,7 +1070,20 @@ int ovs_get_info(ovs_gauge_t g, ovs_apply_info* info, int32_t nrhs) {
         if (stt[r] == OVS_ESIGN) worst = OVS_ESIGN;
         else if (stt[r] == OVS_NOT_CONVERGED && worst == OVS_OK) worst = OVS_NOT_CONVERGED;
     }
+    if (bad_rhs >= 0) {
+        char msg[128];
+        snprintf(msg, sizeof(msg), "right-hand side %d: the source is not finite (NaN or infinity)", bad_rhs);
+        return fail(OVS_EINVAL, msg);
+    }
     return worst;
+}
+
+int ovs_check_wait_timeout(void* stream) {
+    int code = 0;
+    const cudaError_t e = check_wait_timeout((cudaStream_t)stream, &code);
+    if (e != cudaSuccess) return fail(OVS_ECUDA, cudaGetErrorString(e));
+    if (code != OVS_ETIMEOUT) return fail(OVS_ECUDA, "the bounded wait of the self-check did not report a timeout");
+    return OVS_ETIMEOUT;
 }
 
 int ovs_stencil_tuning(ovs_gauge_t g, int32_t prec, int32_t nrhs, int32_t* shape, float* ms) {

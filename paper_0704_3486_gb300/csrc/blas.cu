@@ -469,7 +469,8 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(const double2* __restrict_
     const double uu = rr[2 * j].x;
     const double2 uz = rr[2 * j + 1];
     const double b2 = uu - ss;
-    const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+    // a NaN (from a non-finite source) stays NaN, so that it is reported
+    const double beta = (b2 > 0.0 || isnan(b2)) ? sqrt(b2) : 0.0;
     if (j == 0) {
         if (tid == 0) {
             beta0[r] = beta;

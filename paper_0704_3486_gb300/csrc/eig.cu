@@ -112,6 +112,7 @@ struct Ctx {
         cudaError_t e_ = (call);                                                         \
         if (e_ != cudaSuccess) {                                                         \
             snprintf(c.err, sizeof(c.err), "%s: %s", #call, cudaGetErrorString(e_));     \
+            cudaGetLastError(); /* clear a non-sticky error for later launches */       \
             return e_ == cudaErrorMemoryAllocation ? OVS_ENOMEM : OVS_ECUDA;             \
         }                                                                                \
     } while (0)

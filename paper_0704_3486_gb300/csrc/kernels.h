@@ -119,6 +119,9 @@ cudaError_t launch_recombine_tma(const void* basis, long long basis_rhs_stride, 
                                  const int* Jdev, const void* coef, long long coef_stride, double alpha, void* y,
                                  long long y_rhs_stride, long long nunits, int nrhs, int num_sms, const int* active,
                                  int* err, cudaStream_t st);
+// self-check: a bounded mbarrier wait that can never complete; *code gets
+// the error word it left (OVS_ETIMEOUT when the bound works)
+cudaError_t check_wait_timeout(cudaStream_t st, int* code);
 cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, long long vec_stride, int J,
                                       const void* red, long long red_stride, const double* inv_beta,
                                       const void* dcoef, void* u, long long u_rhs_stride, const void* z,

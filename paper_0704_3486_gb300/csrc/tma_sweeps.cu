@@ -37,7 +37,7 @@ constexpr int TE = 2;
 constexpr int TU = TB * TE;
 constexpr int TNS = 3;
 constexpr size_t kStageBytes = (size_t)TG * TU * 16;
-constexpr long long kWaitLimit = 1LL << 24;  // try_wait polls before giving up
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a wait gives up after 1 s
 constexpr int OVS_ETIMEOUT_CODE = -7;        // OVS_ETIMEOUT
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -66,10 +66,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// try_wait until the phase completes or kWaitNs have passed (the clock is
+// read only once the first try has failed)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (long long n = 0; n < kWaitLimit; ++n)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
 }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -140,11 +150,12 @@ __device__ __forceinline__ bool consumers_sync_or(bool p) {
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TB) : "memory"); }
 // bounded wait that also gives up once another thread has raised `abort`
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
-    for (long long n = 0; n < kWaitLimit; ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (*abort) return false;
+        if (*abort || global_ns() - t0 > kWaitNs) return false;
     }
-    return false;
 }
 // block that owns flattened item i under the contiguous split of T items
 // over G blocks (block q owns [floor(qT/G), floor((q+1)T/G)))
@@ -786,6 +797,29 @@ cudaError_t launch_recombine_tma(const void* basis, long long basis_rhs_stride, 
                                               (const double2*)coef, coef_stride, alpha, (double2*)y, y_rhs_stride,
                                               nunits, nrhs, active, err);
     return cudaGetLastError();
+}
+
+// Self-check of the bounded waits: one thread waits on an mbarrier on which
+// nothing ever arrives; after kWaitNs it records OVS_ETIMEOUT in the error
+// word and returns, as the sweeps do when a copy never lands.
+static __device__ int g_wait_check_err;
+
+__global__ void k_wait_timeout_check() {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        g_wait_check_err = 0;
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        if (!mbar_wait_bounded(&bar, 0)) g_wait_check_err = OVS_ETIMEOUT_CODE;
+    }
+}
+
+cudaError_t check_wait_timeout(cudaStream_t st, int* code) {
+    k_wait_timeout_check<<<1, 32, 0, st>>>();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(code, g_wait_check_err, sizeof(int));
+    return e;
 }
 
 }  // namespace ovs
