@@ -832,9 +832,11 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
                             nrhs, kw.partial, kw.active, st));
         KL(OVS_PROF_SMALL, 16.0 * dblk * S * nrhs,
            launch_reduce(kw.partial, dblk, S, S, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
-        KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 3.0 * j) * nrhs,
+        KL(OVS_PROF_SMALL, 16.0 * 3.0 * j * nrhs,
            launch_arnoldi_step(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.beta, kw.inv_beta, kw.dcoef, kw.hnorm2,
                                kw.active, kw.k_used, nrhs, st));
+        KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 2.0 * j) * nrhs,
+           launch_arnoldi_column(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.inv_beta, kw.dcoef, kw.active, nrhs, st));
         // A7 (batched form): every `every` steps, the sign of the complete
         // H_j of each active right-hand side; stop it once successive
         // coefficient vectors agree to tol (V orthonormal, so this is the

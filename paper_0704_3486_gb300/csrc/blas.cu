@@ -446,7 +446,8 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c, doub
 //  - j = 0: beta is ||x_ominus|| (kept in beta0 for the result);
 //  - column j, first pass: with g = Hbar_{j-1} s (Arnoldi relation
 //    A V_{j-1} = V_j Hbar_{j-1}), H[i][j] = (t_i - g_i)/beta for i < j and
-//    H[j][j] = (u^H z - s^H t)/beta^2 - g_j/beta;
+//    H[j][j] = (u^H z - s^H t)/beta^2 - g_j/beta (k_arnoldi_column, the
+//    O(j^2) part, spread over many blocks);
 //  - the update sweep then needs 1/beta and d = (u^H z - s^H t)/beta^2.
 __global__ void __launch_bounds__(256) k_arnoldi_step(const double2* __restrict__ red, long long red_stride, int j,
                                                       double2* __restrict__ H, long long h_rhs, int ldh,
@@ -513,25 +514,47 @@ __global__ void __launch_bounds__(256) k_arnoldi_step(const double2* __restrict_
     }
     const double ib = 1.0 / beta;
     const double dr = (uz.x - shr) * ib * ib, di = (uz.y - shi) * ib * ib;
-    for (int l = tid; l <= j; l += blockDim.x) {
-        double gr = 0.0, gi = 0.0;
-        for (int i = (l > 0 ? l - 1 : 0); i < j; ++i) {  // H is upper Hessenberg
-            const double2 h = Hr[l + (long long)i * ldh];
-            const double2 si = rr[i];
-            gr += h.x * si.x - h.y * si.y;
-            gi += h.x * si.y + h.y * si.x;
-        }
-        if (l < j) {
-            const double2 ti = rr[j + l];
-            Hr[l + (long long)j * ldh] = make_double2((ti.x - gr) * ib, (ti.y - gi) * ib);
-        } else {
-            Hr[j + (long long)j * ldh] = make_double2(dr - gr * ib, di - gi * ib);
-        }
-    }
     if (tid == 0) {
         inv_beta[r] = ib;
         dcoef[r] = make_double2(dr, di);
         k_used[r] = j + 1;
+    }
+}
+
+// Column j of H, first pass (after k_arnoldi_step of the same j): with
+// g = Hbar_{j-1} s, H[l][j] = (t_l - g_l)/beta for l < j and
+// H[j][j] = d - g_j/beta. One warp per row l: the lanes split the terms of
+// g_l (H is upper Hessenberg, so i >= l - 1) and reduce with shuffles.
+// Grid: x = groups of 8 rows, y = right-hand side.
+__global__ void __launch_bounds__(256) k_arnoldi_column(const double2* __restrict__ red, long long red_stride, int j,
+                                                        double2* __restrict__ H, long long h_rhs, int ldh,
+                                                        const double* __restrict__ inv_beta,
+                                                        const double2* __restrict__ dcoef,
+                                                        const int* __restrict__ active) {
+    const int r = blockIdx.y, lane = threadIdx.x & 31;
+    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (active[r] == 0 || l > j) return;  // stopped (breakdown, zero source) or past the column
+    const double2* rr = red + r * red_stride;
+    double2* Hr = H + r * h_rhs;
+    double gr = 0.0, gi = 0.0;
+    for (int i = (l > 0 ? l - 1 : 0) + lane; i < j; i += 32) {
+        const double2 h = Hr[l + (long long)i * ldh];
+        const double2 si = rr[i];
+        gr += h.x * si.x - h.y * si.y;
+        gi += h.x * si.y + h.y * si.x;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        gr += __shfl_xor_sync(0xffffffffu, gr, off);
+        gi += __shfl_xor_sync(0xffffffffu, gi, off);
+    }
+    if (lane != 0) return;
+    const double ib = inv_beta[r];
+    if (l < j) {
+        const double2 ti = rr[j + l];
+        Hr[l + (long long)j * ldh] = make_double2((ti.x - gr) * ib, (ti.y - gi) * ib);
+    } else {
+        const double2 d = dcoef[r];
+        Hr[j + (long long)j * ldh] = make_double2(d.x - gr * ib, d.y - gi * ib);
     }
 }
 
@@ -659,6 +682,15 @@ cudaError_t launch_arnoldi_step(const void* red, long long red_stride, int j, vo
                                 int* k_used, int nrhs, cudaStream_t st) {
     k_arnoldi_step<<<nrhs, 256, 0, st>>>((const double2*)red, red_stride, j, (double2*)H, h_rhs, ldh, beta0, inv_beta,
                                          (double2*)dcoef, hnorm2, active, k_used);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arnoldi_column(const void* red, long long red_stride, int j, void* H, long long h_rhs, int ldh,
+                                  const double* inv_beta, const void* dcoef, const int* active, int nrhs,
+                                  cudaStream_t st) {
+    const dim3 grid((j + 1 + 7) / 8, nrhs);
+    k_arnoldi_column<<<grid, 256, 0, st>>>((const double2*)red, red_stride, j, (double2*)H, h_rhs, ldh, inv_beta,
+                                           (const double2*)dcoef, active);
     return cudaGetLastError();
 }
 

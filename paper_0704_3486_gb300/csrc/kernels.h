@@ -90,6 +90,10 @@ cudaError_t launch_reduce(const void* partial, int nblk, int pstride, int J, int
 cudaError_t launch_arnoldi_step(const void* red, long long red_stride, int j, void* H, long long h_rhs, int ldh,
                                 double* beta0, double* inv_beta, void* dcoef, double* hnorm2, int* active,
                                 int* k_used, int nrhs, cudaStream_t st);
+// column j of H (the O(j^2) part of the step), after launch_arnoldi_step
+cudaError_t launch_arnoldi_column(const void* red, long long red_stride, int j, void* H, long long h_rhs, int ldh,
+                                  const double* inv_beta, const void* dcoef, const int* active, int nrhs,
+                                  cudaStream_t st);
 // v_j = (u - V s)/beta -> slot J; u <- (z - V t)/beta - v_j d
 cudaError_t launch_arnoldi_update(int prec, void* basis, long long basis_rhs_stride, long long vec_stride, int J,
                                   const void* red, long long red_stride, const double* inv_beta, const void* dcoef,
