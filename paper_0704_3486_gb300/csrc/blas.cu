@@ -3,10 +3,15 @@
 // K5 (LR projection c = L^+ x, x_ominus = x - R c, Sec. 5.3 Eq. xdec).
 //
 // A field is a flat array of 16-byte units (one complex128, or two
-// complex64). Each right-hand side r owns its Krylov basis; a block of 256
-// threads covers one row block of one right-hand side and streams every
-// basis vector through it, so the basis is read once per sweep with fully
-// coalesced 16-byte loads.
+// complex64). Each right-hand side r owns its Krylov basis; in the register
+// sweeps here a block of 256 threads covers one row block of one
+// right-hand side and streams every basis vector through it, so the basis
+// is read once per sweep with fully coalesced 16-byte loads. They serve the
+// complex128 form and the shared-basis projections; the complex64 form's
+// Arnoldi sweeps and recombination are the TMA kernels of tma_sweeps.cu.
+// Also here: the shared-basis combination of the deflated part
+// (k_shared_combine) and the small kernels of each Arnoldi step (partial
+// sums, Hessenberg column, final pass).
 //
 // Precision: in the complex64 form the products and the partial sums of a
 // thread (2*E terms) and of a warp (a 32-lane tree) are FP32; every warp
