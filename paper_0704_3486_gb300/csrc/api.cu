@@ -859,7 +859,17 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
                launch_arnoldi_update(tp, basis, basis_rhs_units, units, j, kw.htmp, kw.jcap, kw.inv_beta, kw.dcoef,
                                      w.xint, units, w.wvec, units, units, plan, nrhs, kw.active, st));
     }
-    {  // second Gram-Schmidt pass of the last column
+    if (tp == PREC_F32 && gdots_chunk_fits(k)) {  // second Gram-Schmidt pass of the last column
+        // the two-vector TMA sweep with z = u: s (and a copy as t), u^H u at 2k
+        const int S = gdots_stride(2, k);
+        KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (k + 1.0),
+           launch_gdots2_chunk(basis, basis_rhs_units, units, k, w.xint, units, w.xint, units, units, nrhs,
+                               g->num_sms, dslots, kw.partial, kw.active, kw.err, st));
+        KL(OVS_PROF_SMALL, 16.0 * dslots * S * nrhs,
+           launch_reduce(kw.partial, dslots, S, S, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
+        KL(OVS_PROF_SMALL, 16.0 * 2.0 * k * nrhs,
+           launch_arnoldi_final(kw.htmp, kw.jcap, k, 2 * k, kw.H, h_rhs, ldh, kw.active, nrhs, st));
+    } else {
         const int S = gdots_stride(1, k);
         KL(OVS_PROF_DOTS, (double)N * sz_of(tp) * nrhs * (k + 1.0),
            launch_gdots(tp, 1, basis, basis_rhs_units, units, k, w.xint, units, nullptr, 0, true, units, plan, nrhs,
@@ -867,7 +877,7 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
            launch_reduce(kw.partial, plan.nblk, S, S, nrhs, kw.htmp, kw.jcap, false, kw.active, st));
         KL(OVS_PROF_SMALL, 16.0 * 2.0 * k * nrhs,
-           launch_arnoldi_final(kw.htmp, kw.jcap, k, kw.H, h_rhs, ldh, kw.active, nrhs, st));
+           launch_arnoldi_final(kw.htmp, kw.jcap, k, k, kw.H, h_rhs, ldh, kw.active, nrhs, st));
     }
     // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v)
     KL(OVS_PROF_NEWTON, 16.0 * (double)k * k * nrhs,

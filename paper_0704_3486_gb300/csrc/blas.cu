@@ -563,10 +563,11 @@ __global__ void __launch_bounds__(256) k_arnoldi_column(const double2* __restric
     }
 }
 
-// Second Gram-Schmidt pass of the last column: red[r] = (s, u^H u, .) from a
-// sweep over V_0..V_{k-1}; H[:k][k-1] += s, H[k][k-1] = ||u - V s||.
+// Second Gram-Schmidt pass of the last column: red[r] holds s at [0, k) and
+// u^H u at entry uu_at, from a sweep over V_0..V_{k-1};
+// H[:k][k-1] += s, H[k][k-1] = ||u - V s||.
 __global__ void __launch_bounds__(256) k_arnoldi_final(const double2* __restrict__ red, long long red_stride, int k,
-                                                       double2* __restrict__ H, long long h_rhs, int ldh,
+                                                       int uu_at, double2* __restrict__ H, long long h_rhs, int ldh,
                                                        const int* __restrict__ active) {
     __shared__ double sh[3 * 8];
     const int r = blockIdx.x, tid = threadIdx.x;
@@ -582,7 +583,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_final(const double2* __restrict
     }
     block_sum3(ss, z1, z2, sh);
     if (tid == 0) {
-        const double b2 = rr[k].x - ss;
+        const double b2 = rr[uu_at].x - ss;
         Hr[k + (long long)(k - 1) * ldh] = make_double2(b2 > 0.0 ? sqrt(b2) : 0.0, 0.0);
     }
 }
@@ -699,9 +700,9 @@ cudaError_t launch_arnoldi_column(const void* red, long long red_stride, int j, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, void* H, long long h_rhs, int ldh,
-                                 const int* active, int nrhs, cudaStream_t st) {
-    k_arnoldi_final<<<nrhs, 256, 0, st>>>((const double2*)red, red_stride, k, (double2*)H, h_rhs, ldh, active);
+cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, int uu_at, void* H, long long h_rhs,
+                                 int ldh, const int* active, int nrhs, cudaStream_t st) {
+    k_arnoldi_final<<<nrhs, 256, 0, st>>>((const double2*)red, red_stride, k, uu_at, (double2*)H, h_rhs, ldh, active);
     return cudaGetLastError();
 }
 

@@ -101,8 +101,9 @@ cudaError_t launch_arnoldi_update(int prec, void* basis, long long basis_rhs_str
                                   long long nunits, const BlasPlan& plan, int nrhs, const int* active,
                                   cudaStream_t st);
 // last column: H[:k][k-1] += s, H[k][k-1] = ||u - V s||
-cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, void* H, long long h_rhs, int ldh,
-                                 const int* active, int nrhs, cudaStream_t st);
+// red[r]: s at [0, k), u^H u at entry uu_at
+cudaError_t launch_arnoldi_final(const void* red, long long red_stride, int k, int uu_at, void* H, long long h_rhs,
+                                 int ldh, const int* active, int nrhs, cudaStream_t st);
 
 // TMA-pipelined complex64 form of the Arnoldi update sweep (tma_sweeps.cu);
 // *err receives OVS_ETIMEOUT if a bounded wait gives up.
