@@ -79,3 +79,21 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.ovs_sign_apply(None, None, None, 1, None, None, None) == -1
     with pytest.raises(ovs.OvsError):
         ovs._check(-1)
+
+
+def test_stencil_shapes_and_trace_classes_match_header():
+    """The binding's shape list is the header's candidate order (the order of
+    the times ovs_stencil_tuning returns), and its trace classes are the
+    header's OVS_PROF_* values in order."""
+    import paper_0704_3486_gb300 as ovs
+    text = open(os.path.join(ROOT, "include", "ovsign.h")).read()
+    block = text[text.index("The 18 candidates are"):text.index("The first stencil launch")]
+    shapes = [tuple(int(v) for v in m) for m in re.findall(r"\((\d+),(\d+),(\d+)\)", block)]
+    assert shapes == ovs.STENCIL_SHAPES and len(shapes) == 18
+    kernels = open(os.path.join(ROOT, "paper_0704_3486_gb300", "csrc", "kernels.h")).read()
+    table = kernels[kernels.index("kStencilShapes[kNumStencilShapes] = {"):]
+    table = table[:table.index("};")]
+    assert [tuple(int(v) for v in m) for m in re.findall(r"\{(\d+), (\d+), (\d+)\}", table)] == shapes
+    classes = re.findall(r"OVS_PROF_([A-Z]+)\s*=\s*(\d+)", text)
+    named = {int(v): n.lower() for n, v in classes if n != "NCLASS"}
+    assert [named[i] for i in range(len(named))] == ovs.PROF_CLASSES

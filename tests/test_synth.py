@@ -38,3 +38,19 @@ def test_vectors_unit_norm():
     assert np.allclose(np.linalg.norm(x, axis=1), 1)
     w = synth.plane_wave_vectors((2, 2, 2, 4), [(1, 0, 0, 1)], 3)
     assert w.shape == (1, 12 * 32) and np.isclose(np.linalg.norm(w), 1)
+
+
+def test_batched_instance_recipe():
+    """Sizes cycle 4^4/6^4/8^4, mu cycles 0.1/0.2/0.3, eps in [0.5, 0.7],
+    right-hand-side counts in 1..16 and uneven, all reproducible."""
+    a = synth.batched_instances(32)
+    assert a == synth.batched_instances(32)
+    for i, d in enumerate(a):
+        assert d["dims"] == [(4, 4, 4, 4), (6, 6, 6, 6), (8, 8, 8, 8)][i % 3]
+        assert d["mu"] == (0.1, 0.2, 0.3)[i % 3]
+        assert 0.5 <= d["eps"] <= 0.7 and 1 <= d["nrhs"] <= 16
+        assert d["gauge_seed"] == 100 + i and d["source_seed"] == 200 + i
+    assert len({d["nrhs"] for d in a}) > 5
+    r, l, lam = synth.synthetic_deflation(96, 7, 3)
+    assert r.shape == (96, 7) and l.shape == (96, 7) and lam.shape == (7,)
+    assert np.all(np.abs(lam.real) >= 0.05) and np.all(np.abs(lam.real) <= 0.5)
