@@ -170,7 +170,8 @@ int ovs_deflate_restore(ovs_gauge_t g, const char* path);
 
 /* Options of a sign application. */
 typedef struct {
-    int32_t k_max;       /* Krylov dimension (Sec. 4 suggests even values) */
+    int32_t k_max;       /* Krylov dimension, 1..790 (Sec. 4 suggests even
+                            values) */
     int32_t check_every; /* 0: run exactly k_max steps (stop only at breakdown);
                             >0 (even): every check_every steps compute
                             c_j = beta sgn(H_j) e_1 and stop a right-hand
@@ -204,7 +205,10 @@ typedef struct {
  * not overlap). If info is not NULL the call waits for the stream and fills
  * nrhs reports; if NULL the call returns once the work is enqueued and
  * ovs_get_info() reads the reports later. Returns the worst per-RHS status
- * when info is given. Errors: EINVAL, ESTATE (mu not set), ENOMEM, ECUDA. */
+ * when info is given. Errors: EINVAL (also: a right-hand side whose source
+ * is not finite, reported when the reports are read), ESTATE (mu not set),
+ * ENOMEM (the handle stays usable), ECUDA, ETIMEOUT (a bounded device wait
+ * gave up; reported when the reports are read). */
 int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
                    ovs_apply_info* info, void* stream);
 
