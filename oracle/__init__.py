@@ -11,15 +11,20 @@ in complex128, no blocking or fusion beyond what each formula states.
 Modules and the passages they follow:
 
 * ``lattice``   -- gamma matrices, D_w(mu) and H_w(mu) = gamma5 D_w(mu) as a
-                   sparse matrix built term by term (Sec. 2, Eq. Dw).
+                   sparse matrix built term by term, and the same sum
+                   evaluated at chosen sites only for large lattices
+                   (Sec. 2, Eq. Dw).
 * ``signfun``   -- complex sign (Sec. 2, Eq. sgnz) and the spectral matrix
                    function f(A) = U f(Lambda) U^-1 (Sec. 2, Eq. fA).
 * ``newton``    -- Roberts' iteration S <- (S + S^-1)/2 (Sec. 5.2, Eq. Roberts).
 * ``arnoldi``   -- Arnoldi recurrence with classical Gram-Schmidt applied
                    twice (Sec. 4, Eqs. Arnoldi, HVAV) and the approximation
-                   f(A)x ~ beta V_k f(H_k) e_1 (Sec. 4, Eq. yproj3).
+                   f(A)x ~ beta V_k f(H_k) e_1 (Sec. 4, Eq. yproj3), at a
+                   fixed k or stopped by the change of the coefficient
+                   vector between checks (the batched form's criterion).
 * ``deflation`` -- LR deflation (Sec. 5.3, Eqs. Rev, Lev, xdec, fAxLR, fARLx,
-                   LRArnoldi, fAxLRArn) and critical eigenpairs (Sec. 6).
+                   LRArnoldi, fAxLRArn), also with the adaptive stop, and
+                   critical eigenpairs (Sec. 6).
 * ``freefield`` -- unit-link (free) closed form of D_w, H_w and sgn(H_w) in
                    momentum space; an independent pin for the above.
 
@@ -27,7 +32,9 @@ Pins (tests marked ``not gpu``): the free-field closed form, gauge
 covariance, gamma5-hermiticity, the Hermitian mu = 0 case (sgn equals the
 polar factor), sgn(A)^2 = I, Arnoldi exactness at the grade of x, Newton
 against scipy.linalg.signm and against matrices of known eigen-decomposition,
-and LR deflation on exact eigenvectors. Parity pinned for every function.
+LR deflation on exact eigenvectors, the per-site sum against the pure-gauge
+closed form, and the adaptive stop against the fixed-k form and the dense
+sign. Parity pinned for every function.
 """
 
 from . import lattice, signfun, newton, arnoldi, deflation, freefield  # noqa: F401
