@@ -388,3 +388,57 @@ def test_lr_adaptive_stop_matches_fixed_k_and_exact():
     assert info["k_used"] < info0["k_used"]
     assert rel(y, ref) < 1e-6
 
+
+
+# ------------------------------------------------ planted mistakes are caught
+def _mutant(module, old, new):
+    """The module's source with one plausible mistake planted (in memory)."""
+    import importlib
+    import types
+    mod = importlib.import_module(f"oracle.{module}")
+    src = open(mod.__file__).read()
+    assert src.count(old) >= 1, old
+    m = types.ModuleType(f"mutant_{module}")
+    m.__package__ = "oracle"
+    exec(compile(src.replace(old, new, 1), mod.__file__, "exec"), m.__dict__)
+    return m
+
+
+@pytest.mark.parametrize("old,new", [
+    ("u = np.conj(np.swapaxes(links[nb, nu], -1, -2))", "u = links[nb, nu]"),          # missing dagger
+    ("bc = np.where(wrapped & (nu == 3), -1.0, 1.0)\n            if step",
+     "bc = np.where(wrapped & (nu == 3), 1.0, 1.0)\n            if step"),           # periodic in time
+    ("w = 1.0 / tfac", "w = tfac"),                                                  # e^{+mu} backward
+    ("proj = one - sign_fwd * gam[nu]\n                u = np.conj",
+     "proj = one + sign_fwd * gam[nu]\n                u = np.conj"),               # projector sign
+])
+def test_stencil_pin_catches_planted_mistakes(old, new):
+    dims = (4, 6, 2, 8)
+    v = int(np.prod(dims))
+    u, om = synth.pure_gauge_links(dims, 23)
+    x = synth.gaussian_vectors(12 * v, 1, 13)[0]
+    ref = freefield.apply_free(x, dims, 0.2, MW, "H", omega=om).reshape(v, 12)
+    bad = _mutant("lattice", old, new).hw_sites(u, dims, 0.2, MW, x, np.arange(v))
+    assert np.abs(bad - ref).max() > 1e-6
+
+
+def test_newton_pin_catches_planted_mistake():
+    a = np.diag([2.0, -0.5, 1.5, -3.0]).astype(np.complex128) + 0.1 * np.triu(np.ones((4, 4)), 1)
+    bad = _mutant("newton", "s_new = 0.5 * (s + np.linalg.inv(s))", "s_new = 0.5 * (s + np.linalg.inv(s).T)")
+    try:
+        s, _ = bad.roberts_sign(a)
+    except Exception:  # a wrong iteration may not converge at all
+        return
+    assert np.abs(s - scipy.linalg.signm(a)).max() > 1e-6
+
+
+def test_deflation_pin_catches_planted_mistake():
+    h, n = _small_problem()
+    hd = h.toarray()
+    dec = signfun.eig_decomposition(hd)
+    lam, r, l = deflation.critical_pairs_dense(hd, n, dec)
+    x = synth.gaussian_vectors(n, 1, 4)[0]
+    ref = signfun.sgn_apply_dense(hd, x, dec)
+    bad = _mutant("deflation", "y_defl = r @ (sgn_re(lam) * c)", "y_defl = r @ (np.abs(sgn_re(lam)) * c)")
+    y, _ = bad.lr_sign_apply(lambda q: h @ q, x, r, l, lam, 2)
+    assert rel(y, ref) > 1e-3
