@@ -18,6 +18,9 @@
 // partial is then added into FP64, so inner products, norms and Hessenberg
 // entries are accumulated in FP64 over the rest of the vector.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -609,20 +612,33 @@ BlasPlan blas_plan(long long nunits, int nrhs, int num_sms) {
     return p;
 }
 
-static bool g_attr_done = false;
+cudaError_t ensure_dyn_smem(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> granted;  // (kernel, device) -> bytes
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = granted[std::make_pair(kernel, dev)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
+// the register sweeps keep their reduction buffers (up to 200 KB) in
+// dynamic shared memory
 static void set_smem_attrs() {
-    if (g_attr_done) return;
-    const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_gdots<double, 1, 16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_gdots<double, 2, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_gdots<float, 1, 16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_gdots<float, 2, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_arnoldi_update<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_arnoldi_update<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_update<double, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_update<float, float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_update<float, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    g_attr_done = true;
+    const size_t big = 200 * 1024;
+    ensure_dyn_smem((const void*)k_gdots<double, 1, 16, 4>, big);
+    ensure_dyn_smem((const void*)k_gdots<double, 2, 8, 4>, big);
+    ensure_dyn_smem((const void*)k_gdots<float, 1, 16, 4>, big);
+    ensure_dyn_smem((const void*)k_gdots<float, 2, 8, 4>, big);
+    ensure_dyn_smem((const void*)k_arnoldi_update<double, 2>, big);
+    ensure_dyn_smem((const void*)k_arnoldi_update<float, 2>, big);
+    ensure_dyn_smem((const void*)k_update<double, double, 2>, big);
+    ensure_dyn_smem((const void*)k_update<float, float, 2>, big);
+    ensure_dyn_smem((const void*)k_update<float, double, 2>, big);
 }
 
 int gdots_stride(int nw, int J) { return nw * J + 2; }

@@ -11,6 +11,10 @@ struct Geom;
 
 enum { PREC_F64 = 0, PREC_F32 = 1 };
 
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device
+// (once per kernel, device and size; thread safe).
+cudaError_t ensure_dyn_smem(const void* kernel, size_t bytes);
+
 // ---- K1 / K7 (dslash.cu)
 // Shape of a stencil launch: `rt` right-hand sides per thread (1 or 2), a
 // block of `sites` sites (threadIdx.x) times `rb` right-hand-side tiles

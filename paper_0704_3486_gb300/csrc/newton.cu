@@ -18,6 +18,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "common.cuh"
@@ -504,23 +505,23 @@ constexpr size_t kClusterSmemMax = 220 * 1024;
 // and is asked of the runtime (cached per size and shared-memory need).
 static int pick_cluster(int kmax, int nrhs) {
     static std::mutex mu;
-    static std::map<std::pair<int, size_t>, int> resident;
-    static bool attr = false;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_newton_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kClusterSmemMax) != cudaSuccess) {
-            cudaGetLastError();
-            return 0;
-        }
-        attr = true;
+    static std::map<std::tuple<int, int, size_t>, int> resident;  // (device, size, smem) -> clusters
+    if (ensure_dyn_smem((const void*)k_newton_cluster, kClusterSmemMax) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lock(mu);
     int best = 0;
     double best_cost = 0.0;
     for (int ncl : kClusterSizes) {
         const size_t need = cluster_smem(kmax, ncl);
         if (need > kClusterSmemMax) continue;
-        auto key = std::make_pair(ncl, need);
+        auto key = std::make_tuple(dev, ncl, need);
         auto it = resident.find(key);
         if (it == resident.end()) {
             cudaLaunchConfig_t cfg = {};
@@ -577,12 +578,8 @@ cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const 
                                   n_fixed);
     }
     const size_t smem = (size_t)kmax * 2 * sizeof(cd) + (size_t)kmax * sizeof(int);
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_newton, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const cudaError_t e = ensure_dyn_smem((const void*)k_newton, 200 * 1024);
+    if (e != cudaSuccess) return e;
     k_newton<<<nrhs, NT, smem, st>>>((const double2*)H, h_rhs_stride, ldh, k_used, beta, (double2*)coeff,
                                      coeff_stride, (double2*)work, kmax, iters, status, active, n_fixed);
     return cudaGetLastError();

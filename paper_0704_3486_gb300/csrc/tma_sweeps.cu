@@ -739,14 +739,9 @@ cudaError_t launch_gdots2_chunk(const void* basis, long long basis_rhs_stride, l
                                 const void* u, long long u_rhs_stride, const void* z, long long z_rhs_stride,
                                 long long nunits, int nrhs, int num_sms, int nslot, void* partial, const int* active,
                                 int* err, cudaStream_t st) {
-    static size_t set = 0;
     const size_t smem = gdots_chunk_smem(J);
-    if (smem > set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_gdots2_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        set = smem;
-    }
+    const cudaError_t e = ensure_dyn_smem((const void*)k_gdots2_ws, smem);
+    if (e != cudaSuccess) return e;
     if (nslot != gdots_chunk_slots(nunits, nrhs, num_sms)) return cudaErrorInvalidValue;
     const int G = gdots_chunk_grid(nunits, nrhs, num_sms);
     k_gdots2_ws<<<G, DTHREADS, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J, (const float4*)u,
@@ -760,14 +755,9 @@ cudaError_t launch_arnoldi_update_tma(void* basis, long long basis_rhs_stride, l
                                       const void* dcoef, void* u, long long u_rhs_stride, const void* z,
                                       long long z_rhs_stride, long long nunits, int nrhs, int num_sms,
                                       const int* active, int* err, cudaStream_t st) {
-    static size_t set = 0;
     const size_t smem = TNS * kStageBytes + (size_t)(2 * J + 1) * sizeof(cf);
-    if (smem > set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_arnoldi_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        set = smem;
-    }
+    const cudaError_t e = ensure_dyn_smem((const void*)k_arnoldi_update_ws, smem);
+    if (e != cudaSuccess) return e;
     const long long T = (nunits + TU - 1) / TU * nrhs;
     const int G = (int)std::max<long long>(1, std::min<long long>(num_sms, T));
     k_arnoldi_update_ws<<<G, DTHREADS, smem, st>>>((float4*)basis, basis_rhs_stride, vec_stride, J,
@@ -783,14 +773,9 @@ cudaError_t launch_recombine_tma(const void* basis, long long basis_rhs_stride, 
                                  const int* Jdev, const void* coef, long long coef_stride, double alpha, void* y,
                                  long long y_rhs_stride, long long nunits, int nrhs, int num_sms, const int* active,
                                  int* err, cudaStream_t st) {
-    static size_t set = 0;
     const size_t smem = TNS * kStageBytes + (size_t)std::max(J, 1) * sizeof(cf);
-    if (smem > set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_recombine_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        set = smem;
-    }
+    const cudaError_t e = ensure_dyn_smem((const void*)k_recombine_ws, smem);
+    if (e != cudaSuccess) return e;
     const long long T = (nunits + TU - 1) / TU * nrhs;
     const int G = (int)std::max<long long>(1, std::min<long long>(num_sms, T));
     k_recombine_ws<<<G, DTHREADS, smem, st>>>((const float4*)basis, basis_rhs_stride, vec_stride, J, Jdev,
