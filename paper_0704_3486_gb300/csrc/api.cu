@@ -739,8 +739,11 @@ static int check_apply(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts) {
 
 // Enqueue the whole application on st, from the device canonical input xd
 // to the device canonical output yd. Buffers must already be sized
-// (ensure_vec / ensure_kry); no allocation and no host synchronisation
-// happen here, so the sequence can be recorded as a CUDA graph.
+// (ensure_vec / ensure_kry); no allocation happens here, and no host
+// synchronisation except the stencil autotuner's one-time timing of a new
+// (precision, nrhs) pair, which is skipped during stream capture (the
+// batched form tunes before it records), so the sequence can be recorded as
+// a CUDA graph.
 static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, const ovs_apply_opts* opts,
                            cudaStream_t st) {
     const int k = opts->k_max;
