@@ -1,8 +1,9 @@
 // TMA-pipelined sweeps over the complex64 Arnoldi basis: the inner products
-// (K1 dots) and the update (K2) of the delayed-reorthogonalisation step.
+// and the update of the delayed-reorthogonalisation step (K2), and the
+// recombination y += V_k c (K4); also the self-check of the bounded waits.
 //
-// Both sweeps stream the whole basis of every right-hand side once per
-// Arnoldi step, so they are bound by HBM bandwidth. Both are persistent
+// The sweeps stream the whole basis of every right-hand side, so they are
+// bound by HBM bandwidth. All three are persistent
 // (one block per SM) and warp-specialised: one producer lane moves basis
 // tiles into shared memory with 1D bulk asynchronous copies (cp.async.bulk,
 // completion counted in bytes on an mbarrier), 3 stages of 8 vectors x 512
