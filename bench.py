@@ -348,7 +348,7 @@ def run_ours(args, w, world, rank, local):
     # class (16^3x32, 2 RHS, J = 30; profiles/) gave traffic / algorithmic
     # bytes; traffic grows in proportion to the vectors read, so a launch of
     # the timed step moves that ratio times its algorithmic bytes.
-    traffic_ratio = {"dots": 808.94 / 805.31, "update": 851.15 / 855.64}.get(top)
+    traffic_ratio = {"dots": 808.41 / 805.31, "update": 848.11 / 855.64}.get(top)
     per_launch = prof[top]["bytes"] / max(prof[top]["launches"], 1)
     traffic = round(per_launch * traffic_ratio) if traffic_ratio else None
     share = {c: round(prof[c]["ms"] / max(sum(p["ms"] for p in prof.values()), 1e-9), 4) for c in prof}
