@@ -25,16 +25,28 @@ Modules and the passages they follow:
 * ``deflation`` -- LR deflation (Sec. 5.3, Eqs. Rev, Lev, xdec, fAxLR, fARLx,
                    LRArnoldi, fAxLRArn), also with the adaptive stop, and
                    critical eigenpairs (Sec. 6).
+* ``schur``     -- Schur deflation (Sec. 5.2, Eqs. pSd, modArnoldi, newH,
+                   f_H, SylvEq, formula) with the row-by-row Sylvester
+                   solver of App. A (Eqs. GenSylvEq to abij).
+* ``overlap``   -- D_ov(mu) = 1 + gamma5 sgn(H_w(mu)) (Sec. 2, Eqs. Dov,
+                   GW:eq) and restarted GMRES for the nested inversion the
+                   paper names as the method's use (Secs. 6, 7).
 * ``freefield`` -- unit-link (free) closed form of D_w, H_w and sgn(H_w) in
                    momentum space; an independent pin for the above.
+
+``arnoldi`` also holds the harmonic (see-saw-free) variant of Sec. 4.
 
 Pins (tests marked ``not gpu``): the free-field closed form, gauge
 covariance, gamma5-hermiticity, the Hermitian mu = 0 case (sgn equals the
 polar factor), sgn(A)^2 = I, Arnoldi exactness at the grade of x, Newton
 against scipy.linalg.signm and against matrices of known eigen-decomposition,
 LR deflation on exact eigenvectors, the per-site sum against the pure-gauge
-closed form, and the adaptive stop against the fixed-k form and the dense
-sign. Parity pinned for every function.
+closed form, the adaptive stop against the fixed-k form and the dense sign,
+the ARPACK critical pairs against the dense spectral projector, the App. A
+solver against scipy's Sylvester solver and the spectral sign of the
+composite matrix, harmonic Ritz values against their Petrov-Galerkin
+definition, the Ginsparg-Wilson relation and GMRES against a dense solve.
+Parity pinned for every function.
 """
 
-from . import lattice, signfun, newton, arnoldi, deflation, freefield  # noqa: F401
+from . import lattice, signfun, newton, arnoldi, deflation, freefield, schur, overlap  # noqa: F401

@@ -11,6 +11,11 @@ Readings where the paper is silent:
   h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2, column = h1 + h2;
 * breakdown: if H_(j+1,j) <= 1e-12 ||H_(1:j+1,1:j)||_F the Krylov space is
   invariant, the recurrence stops and k_used = j (the result is then exact);
+* harmonic variant (the see-saw-free form the paper cites in Sec. 4, from
+  harmonic Ritz values): f(H_k) is replaced by f(H^_k) with
+  H^_k = H_k + |h_(k+1,k)|^2 H_k^-H e_k e_k^T, whose eigenvalues are the
+  harmonic Ritz values of A on K_k (the theta with A V y - theta V y
+  orthogonal to A K_k);
 * stopping by convergence (batched form; the paper fixes k instead): every
   `every` (even) steps form c_j = beta sgn(H_j) e_1 and stop at the first j
   with ||c_j - c_(j-every)|| / ||c_j|| < tol (c padded with zeros); as V is
@@ -55,8 +60,28 @@ def arnoldi(matvec, x, k):
     return v, h, beta, k
 
 
-def arnoldi_sign(matvec, x, k, **newton_kw):
-    """beta V_k sgn(H_k) e_1 (Eq. yproj3 with f = sgn).
+def harmonic_matrix(h):
+    """H^_k = H_k + |h_(k+1,k)|^2 H_k^-H e_k e_k^T from Hbar_k ((k+1) x k).
+
+    The Petrov-Galerkin condition (A V_k - theta V_k) y orthogonal to A V_k
+    with A V_k = V_(k+1) Hbar_k reads Hbar_k^H Hbar_k y = theta H_k^H y, and
+    Hbar_k^H Hbar_k = H_k^H H_k + |h_(k+1,k)|^2 e_k e_k^T.
+    """
+    k = h.shape[1]
+    hk = np.array(h[:k, :k], dtype=np.complex128)
+    sub = h[k, k - 1] if h.shape[0] > k else 0.0
+    if sub == 0.0:
+        return hk
+    ek = np.zeros(k, dtype=np.complex128)
+    ek[-1] = 1.0
+    f = np.linalg.solve(hk.conj().T, ek)
+    hk[:, -1] += abs(sub) ** 2 * f
+    return hk
+
+
+def arnoldi_sign(matvec, x, k, harmonic=False, **newton_kw):
+    """beta V_k sgn(H_k) e_1 (Eq. yproj3 with f = sgn); with ``harmonic``,
+    beta V_k sgn(H^_k) e_1 (the harmonic variant above).
 
     Returns (y, info) with info = dict(k_used, beta, newton_iters, coeff).
     """
@@ -64,7 +89,8 @@ def arnoldi_sign(matvec, x, k, **newton_kw):
     if k_used == 0:
         return np.zeros_like(np.asarray(x, dtype=np.complex128)), dict(
             k_used=0, beta=beta, newton_iters=0, coeff=np.zeros(0, np.complex128))
-    s, it = roberts_sign(h[:k_used, :k_used], **newton_kw)
+    hk = harmonic_matrix(h[: k_used + 1, :k_used]) if harmonic else h[:k_used, :k_used]
+    s, it = roberts_sign(hk, **newton_kw)
     coeff = beta * s[:, 0]
     y = v[:, :k_used] @ coeff
     return y, dict(k_used=k_used, beta=beta, newton_iters=it, coeff=coeff, H=h)
