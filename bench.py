@@ -50,12 +50,17 @@ def parse_args():
     p.add_argument("--nrhs", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-long-ref", action="store_true", help="skip the FP64 k=790 reference of right-hand side 0")
     p.add_argument("--stencil-shape", type=int, nargs=3, default=None, metavar=("RT", "SITES", "RB"),
                    help="pin the stencil launch shape of the mixed form instead of autotuning it")
     p.add_argument("--workload", choices=["single", "batched"], default="single",
                    help="batched: the multi-instance recipe (32 instances of 4^4/6^4/8^4, m = 20 each, "
                         "per-vector convergence stop) in one ovs_sign_apply_batched call; its own JSON line")
     p.add_argument("--instances", type=int, default=32)
+    p.add_argument("--full-application", action="store_true",
+                   help="with --impl reference: time one complete oracle application instead of samples")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched multi-instance sub-measurement of the default line")
     return p.parse_args()
 
 
@@ -174,59 +179,70 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU baseline
-def cpu_sample(w, k_sample, seed_offset=0):
-    """Time the oracle on a bounded sample of one application and scale it.
+class CpuSample:
+    """The oracle on a bounded sample of one application, and its scaling.
 
     Sample: one right-hand side of the full lattice; the oracle's LR
     deflation with m random (biorthonormalised) vectors and its CGS2
     Arnoldi run for k_sample steps. The matvec and Gram-Schmidt costs are
     measured separately and scaled to k steps as t = t0 + k t_mv +
     c k(k+1)/2 (CGS2 sweeps grow linearly with the step), the Newton cost
-    as (k / k_sample)^3. Returns (seconds per application, description).
+    as (k / k_sample)^3. The operator is built once (not timed).
     """
-    import numpy as np
 
-    import synth
-    from oracle import deflation, lattice, newton
+    def __init__(self, w, k_sample=8):
+        import numpy as np
 
-    links = synth.gauge_links(w["dims"], w["seed"], w["eps"])
-    h = lattice.hw_operator(links, w["dims"], w["mu"], w["m_w"])
-    n = w["N"]
-    rng = np.random.default_rng(1234 + seed_offset)
-    m = w["m"]
-    r = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
-    l_ = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
-    lam = rng.standard_normal(m) + 0.5j * rng.standard_normal(m) if m else None
-    x = synth.gaussian_vectors(n, 1, w["src_seed"] + seed_offset)[0]
-    t_mv = [0.0]
+        import synth
+        from oracle import lattice
 
-    def mv(v):
-        t = time.perf_counter()
-        out = h @ v
-        t_mv[0] += time.perf_counter() - t
-        return out
+        self.w, self.ks = w, k_sample
+        links = synth.gauge_links(w["dims"], w["seed"], w["eps"])
+        self.h = lattice.hw_operator(links, w["dims"], w["mu"], w["m_w"])
+        n, m = w["N"], w["m"]
+        rng = np.random.default_rng(1234)
+        self.r = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
+        self.l = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
+        self.lam = rng.standard_normal(m) + 0.5j * rng.standard_normal(m) if m else None
 
-    t0 = time.perf_counter()
-    _, info = deflation.lr_sign_apply(mv, x, r, l_, lam, k_sample)
-    total = time.perf_counter() - t0
-    tn = time.perf_counter()
-    newton.roberts_sign(info["H"][:k_sample, :k_sample])
-    t_newton = time.perf_counter() - tn
-    ks, k = k_sample, w["k"]
-    per_mv = t_mv[0] / ks
-    t_cgs = max(total - t_mv[0] - t_newton, 0.0)
-    # deflation projection: two sweeps of m vectors plus biorthonormalisation,
-    # measured apart from the Arnoldi loop by a second call with k = 1
-    t1 = time.perf_counter()
-    deflation.lr_sign_apply(lambda v: h @ v, x, r, l_, lam, 1)
-    t_setup = time.perf_counter() - t1 - per_mv
-    t_cgs_loop = max(t_cgs - t_setup, 0.0)
-    c = t_cgs_loop / (ks * (ks + 1) / 2)
-    t_app = t_setup + k * per_mv + c * k * (k + 1) / 2 + t_newton * (k / ks) ** 3
-    desc = (f"1 RHS of the full lattice: LR projection (m={m}) + {ks} of {k} CGS2 Arnoldi steps "
-            f"timed ({total:.1f} s), scaled to k={k} as t0 + k*t_mv + c*k(k+1)/2 "
-            f"(t_mv={per_mv:.3f} s, c={c:.2e} s); numpy/scipy FP64")
-    return t_app, desc
+    def run(self, seed_offset=0):
+        """One sample. Returns (modelled seconds per application, measured
+        seconds of the sample, description)."""
+        import synth
+        from oracle import deflation, newton
+
+        w, h, ks, k, m = self.w, self.h, self.ks, self.w["k"], self.w["m"]
+        x = synth.gaussian_vectors(w["N"], 1, w["src_seed"] + seed_offset)[0]
+        t_mv = [0.0]
+
+        def mv(v):
+            t = time.perf_counter()
+            out = h @ v
+            t_mv[0] += time.perf_counter() - t
+            return out
+
+        t_start = time.perf_counter()
+        t0 = time.perf_counter()
+        _, info = deflation.lr_sign_apply(mv, x, self.r, self.l, self.lam, ks)
+        total = time.perf_counter() - t0
+        tn = time.perf_counter()
+        newton.roberts_sign(info["H"][:ks, :ks])
+        t_newton = time.perf_counter() - tn
+        per_mv = t_mv[0] / ks
+        t_cgs = max(total - t_mv[0] - t_newton, 0.0)
+        # deflation projection: two sweeps of m vectors plus biorthonormalisation,
+        # measured apart from the Arnoldi loop by a second call with k = 1
+        t1 = time.perf_counter()
+        deflation.lr_sign_apply(lambda v: h @ v, x, self.r, self.l, self.lam, 1)
+        t_setup = time.perf_counter() - t1 - per_mv
+        t_sample = time.perf_counter() - t_start
+        t_cgs_loop = max(t_cgs - t_setup, 0.0)
+        c = t_cgs_loop / (ks * (ks + 1) / 2)
+        t_app = t_setup + k * per_mv + c * k * (k + 1) / 2 + t_newton * (k / ks) ** 3
+        desc = (f"1 RHS of the full lattice: LR projection (m={m}) + {ks} of {k} CGS2 Arnoldi steps "
+                f"timed ({total:.1f} s), the application's time MODELLED from it as t0 + k*t_mv + c*k(k+1)/2 "
+                f"(t_mv={per_mv:.3f} s, c={c:.2e} s); numpy/scipy FP64")
+        return t_app, t_sample, desc
 
 
 def cpu_cores():
@@ -277,43 +293,71 @@ def run_ours(args, w, world, rank, local):
     for _ in range(args.warmup):
         ovs.sign_apply(g, x, y, k, prec=ovs.MIXED, stream=stream, want_info=False)
     torch.cuda.synchronize()
-    ovs.profile_enable(g, timing=True)
+
+    def timed_steps(timing):
+        """args.steps applications between a barrier and two CUDA events on
+        the launching stream; per-launch event tracing on or off."""
+        ovs.profile_enable(g, timing=timing)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ovs.sign_apply(g, x, y, k, prec=ovs.MIXED, stream=stream, want_info=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return e0.elapsed_time(e1), ovs.profile_read(g)
+
+    # the timed region: launches counted, no per-launch events
     clocks = ClockSampler(local)
     clocks.start()
-    barrier(world)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ovs.sign_apply(g, x, y, k, prec=ovs.MIXED, stream=stream, want_info=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
+    ms_total, prof_count = timed_steps(False)
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    prof = ovs.profile_read(g)
-    ovs.profile_enable(g, timing=False)
     status, info = ovs.get_info(g, w["nrhs"])
     ms_max = max_over_ranks(ms_total, world, dev)
     value = job_value(w["nrhs"], args.steps, world, ms_max)
+    # the same steps again with every launch bracketed by CUDA events: the
+    # per-class device times of the roofline, and the cost of the tracing
+    ms_traced, prof = timed_steps(True)
+    ovs.profile_enable(g, timing=False)
+    traced_value = job_value(w["nrhs"], args.steps, world, max_over_ranks(ms_traced, world, dev))
+    y_mixed = y.clone()
 
-    # plain FP64, one right-hand side, same (m, k): time it and check the
-    # mixed result of that right-hand side against it
-    x0 = x[:1].contiguous()
-    y64 = torch.empty_like(x0)
-    ovs.sign_apply(g, x0, y64, k, prec=ovs.F64, stream=stream, want_info=False)
+    # plain FP64, one right-hand side per call, same (m, k), for every
+    # right-hand side of the batch: its throughput, and the error of each
+    # mixed result against it
+    y64 = torch.empty_like(x[:1])
+    ovs.sign_apply(g, x[:1].contiguous(), y64, k, prec=ovs.F64, stream=stream, want_info=False)
     torch.cuda.synchronize()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    n64 = 2
-    f0.record(stream)
-    for _ in range(n64):
-        ovs.sign_apply(g, x0, y64, k, prec=ovs.F64, stream=stream, want_info=False)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    fp64_value = n64 / (f0.elapsed_time(f1) / 1e3)
-    rel_err = float(torch.linalg.norm(y[0] - y64[0]) / torch.linalg.norm(y64[0]))
+    rel_errs, ms64 = [], 0.0
+    for r in range(w["nrhs"]):
+        xr = x[r:r + 1].contiguous()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ovs.sign_apply(g, xr, y64, k, prec=ovs.F64, stream=stream, want_info=False)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 += f0.elapsed_time(f1)
+        rel_errs.append(float(torch.linalg.norm(y_mixed[r] - y64[0]) / torch.linalg.norm(y64[0])))
+    fp64_value = w["nrhs"] / (ms64 / 1e3)
+    rel_err = max(rel_errs)
+    # Krylov truncation at k on this basis: the FP64 result at the largest
+    # supported Krylov dimension for right-hand side 0 (a longer reference on
+    # the same deflation; not an exact sign when the basis is not converged)
+    long_ref = None
+    if not args.no_long_ref:
+        k_long = 790
+        ovs.sign_apply(g, x[:1].contiguous(), y64, k_long, prec=ovs.F64, stream=stream, want_info=False)
+        y_k64 = torch.empty_like(y64)
+        ovs.sign_apply(g, x[:1].contiguous(), y_k64, k, prec=ovs.F64, stream=stream, want_info=False)
+        torch.cuda.synchronize()
+        nrm = torch.linalg.norm(y64[0])
+        long_ref = {"k_long": k_long,
+                    "rel_diff_fp64_k_vs_k_long": float(torch.linalg.norm(y_k64[0] - y64[0]) / nrm),
+                    "rel_diff_mixed_k_vs_k_long": float(torch.linalg.norm(y_mixed[0] - y64[0]) / nrm)}
 
     # end to end through the C ABI with pinned host buffers: H2D of x and
     # D2H of y inside the timed region (the library stages host pointers)
@@ -321,6 +365,8 @@ def run_ours(args, w, world, rank, local):
     if not args.no_e2e:
         xh = torch.from_numpy(x_host).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
+        # one untimed call: the FP64 runs above resized the work space
+        ovs.sign_apply(g, xh, yh, k, prec=ovs.MIXED, stream=stream, want_info=False)
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -357,22 +403,28 @@ def run_ours(args, w, world, rank, local):
                                             "matvec": "k_wilson (H_w stencil)"}[top],
                 "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                 "peak_source": f"{peak_src} hbm_gbs (copy)", "traffic": traffic,
+                "measured_in": "a second timed pass of the same steps with per-launch CUDA events",
                 "algorithmic_bytes_per_launch": round(per_launch),
                 "per_class": {c: {"ms_per_step": round(prof[c]["ms"] / args.steps, 3),
                                   "launches_per_step": prof[c]["launches"] // max(args.steps, 1),
                                   "gbs": round(prof[c]["bytes"] / (prof[c]["ms"] / 1e3) / 1e9, 1)
                                   if prof[c]["ms"] > 0 else None,
                                   "share": share[c]} for c in prof}}
-    launches = sum(p["launches"] for p in prof.values())
+    launches = sum(p["launches"] for p in prof_count.values())
 
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(w, world),
-        "fp64_single_rhs": {"value": round(fp64_value, 4), "unit": UNIT, "rel_err_mixed_vs_fp64": rel_err,
+        "fp64_single_rhs": {"value": round(fp64_value, 4), "unit": UNIT, "applications_timed": w["nrhs"],
+                            "rel_err_mixed_vs_fp64": rel_err,
+                            "rel_err_mixed_vs_fp64_per_rhs": [float(f"{e:.3e}") for e in rel_errs],
                             "within_1e-6": rel_err <= 1e-6,
                             "speedup_mixed_batched": round(value / world / fp64_value, 3)},
+        "long_reference": long_ref,
+        "tracing": {"value_with_per_launch_events": round(traced_value, 4),
+                    "overhead_frac": round(1.0 - traced_value / value, 4)},
         "deflation_setup": setup,
         "apply_info": {"k_used": sorted({i["k_used"] for i in info}),
                        "newton_iters": sorted({i["newton_iters"] for i in info}),
@@ -388,7 +440,7 @@ def run_ours(args, w, world, rank, local):
     return out
 
 
-def run_batched(args, world, rank, local):
+def run_batched(args, world, rank, local, steps, warmup):
     """The batched multi-instance workload: synth.batched_instances recipe,
     device set-up of 20 deflation vectors per instance (1 s budget each),
     one ovs_sign_apply_batched of all instances with the per-vector stop
@@ -423,14 +475,14 @@ def run_batched(args, world, rank, local):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=ovs.MIXED, check_every=every, tol=tol, want_info=False)
     torch.cuda.synchronize()
     barrier(world)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=ovs.MIXED, check_every=every, tol=tol, want_info=False)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -452,8 +504,8 @@ def run_batched(args, world, rank, local):
         off += sp["nrhs"]
     out = {
         "metric": "batched sgn(H_w(mu))x applications/s, multi-instance recipe, per-vector stop",
-        "value": round(job_value(total, args.steps, world, ms_max), 3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
+        "value": round(job_value(total, steps, world, ms_max), 3), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": round(ms_max / steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{len(specs)} instances (4^4/6^4/8^4 cycle, mu 0.1/0.2/0.3), "
                                f"{total} RHS, m={m} each, stop at {tol} every {every} steps, cap k={k_cap}",
@@ -468,23 +520,50 @@ def run_batched(args, world, rank, local):
     return out
 
 
+def run_reference_full(w):
+    """One complete oracle application (no sampling, no model): one
+    right-hand side, LR deflation with m seeded random vectors, CGS2 Arnoldi
+    to k, Roberts' iteration on H_k, recombination. Checks the cost model of
+    the bounded sample; its time is the measured one."""
+    sampler = CpuSample(w)
+    import synth
+    from oracle import deflation
+    x = synth.gaussian_vectors(w["N"], 1, w["src_seed"])[0]
+    t0 = time.perf_counter()
+    _, info = deflation.lr_sign_apply(lambda v: sampler.h @ v, x, sampler.r, sampler.l, sampler.lam, w["k"])
+    t_app = time.perf_counter() - t0
+    t_model, _, _ = sampler.run()
+    return {"impl": "reference", "kind": "full_application", "config": config_of(w, 1),
+            "seconds_per_application": round(t_app, 2), "applications_per_s": 1.0 / t_app,
+            "modelled_seconds_per_application": round(t_model, 2), "cores": cpu_cores(),
+            "newton_iters": info["newton_iters"]}
+
+
 def run_reference(args, w, world, rank):
-    """CPU oracle on bounded samples; rank 0 only (other ranks exit)."""
+    """CPU oracle on bounded samples; rank 0 only (other ranks exit).
+
+    Each step runs one bounded sample (CpuSample) and takes its measured
+    wall time as the step's time; the fraction of an application a sample
+    covers comes from the sample's cost model, so value = fraction / step
+    time = 1 / (modelled seconds per application)."""
     if rank != 0:
         return None
-    k_sample = 8
-    times = []
+    sampler = CpuSample(w)
+    t_apps, t_steps = [], []
     desc = ""
     for i in range(args.warmup + args.steps):
-        t_app, desc = cpu_sample(w, k_sample, seed_offset=i)
+        t_app, t_sample, desc = sampler.run(seed_offset=i)
         if i >= args.warmup:
-            times.append(t_app)
-    t = statistics.median(times)
-    value = 1.0 / t
+            t_apps.append(t_app)
+            t_steps.append(t_sample)
+    t_app = statistics.median(t_apps)
+    t_step = statistics.median(t_steps)
+    value = 1.0 / t_app
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w, 1),
+        "applications_per_step": t_step / t_app,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -495,12 +574,12 @@ def main():
     w = workload(args)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
-        out = run_reference(args, w, world, rank)
+        out = run_reference_full(w) if args.full_application and rank == 0 else run_reference(args, w, world, rank)
         if out is not None:
             print(json.dumps(out), flush=True)
         return
     if args.workload == "batched":
-        out = run_batched(args, world, rank, local)
+        out = run_batched(args, world, rank, local, args.steps, args.warmup)
         if rank == 0:
             print(json.dumps(out), flush=True)
         if world > 1:
@@ -508,9 +587,13 @@ def main():
             dist.destroy_process_group()
         return
     out = run_ours(args, w, world, rank, local)
+    if not args.no_batched:
+        b = run_batched(args, world, rank, local, steps=1, warmup=1)
+        out["batched"] = {key: b[key] for key in ("metric", "value", "unit", "steps", "warmup", "ms_per_step",
+                                                  "config", "k_used", "rel_err_mixed_vs_fp64_at_equal_k")}
     if rank == 0:
         if not args.no_cpu_baseline:
-            t_app, desc = cpu_sample(w, 8)
+            t_app, t_sample, desc = CpuSample(w).run()
             out["cpu_baseline"] = {"value": 1.0 / t_app, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                                    "sample": desc}
         print(json.dumps(out), flush=True)

@@ -8,7 +8,10 @@
  * LR deflation of critical eigenvectors (Sec. 5.3, Eq. fAxLRArn), an
  * Arnoldi basis of the deflated Krylov space (Sec. 4, Eq. Arnoldi) and the
  * sign of the small Hessenberg matrix by Roberts' Newton iteration
- * (Sec. 5.2, Eq. Roberts).
+ * (Sec. 5.2, Eq. Roberts). Also: Schur deflation with the Sylvester solver
+ * of App. A (Sec. 5.2), the harmonic (see-saw-free) variant of Sec. 4, and
+ * the overlap operator D_ov(mu) = 1 + gamma5 sgn(H_w(mu)) (Sec. 2, Eq. Dov)
+ * with its nested inversion.
  *
  * Conventions used throughout
  * ---------------------------
@@ -162,9 +165,33 @@ int ovs_deflate_load(ovs_gauge_t g, int32_t m, const double* R, const double* L,
  * m_out receives m. Synchronises the device. */
 int ovs_deflate_get(ovs_gauge_t g, int32_t* m_out, double* R, double* L, double* lambda);
 
-/* Save / restore the deflation basis to a binary file (header with dims,
+/* Schur deflation (Sec. 5.2). Install it from m right eigenvectors of
+ * H_w(mu) given by the caller (host complex128 [m][N], in the order their
+ * Schur vectors are to take): S_m = orthonormal basis of their span with
+ * the leading columns spanning the leading vectors (Cholesky QR, twice),
+ * T_m = S_m^H H_w S_m with its strictly lower part (the eigenvectors'
+ * residual) dropped, and sgn(T_m) by Roberts' iteration on the device
+ * (Sec. 5.2 steps i-ii). Replaces any installed basis; m = 0 removes
+ * deflation. ovs_deflate_get then returns S_m as R and diag(T_m) as lambda.
+ * Errors: EINVAL (dependent vectors), ESTATE (mu not set), ESIGN (an
+ * eigenvalue on the imaginary axis), ENOMEM, ECUDA. */
+int ovs_deflate_load_schur(ovs_gauge_t g, int32_t m, const double* R);
+
+/* ovs_deflate_setup for Schur deflation: the right eigenvectors only (the
+ * paper's reason for the scheme: about half the set-up of LR deflation,
+ * Sec. 5.4), the m of smallest |Re lambda| among the converged pairs, then
+ * installed as by ovs_deflate_load_schur. ovs_set_setup_budget's limit
+ * applies to the one iteration. Errors as ovs_deflate_setup. */
+int ovs_deflate_setup_schur(ovs_gauge_t g, int32_t m, double tol, double* eig_out);
+
+/* Scheme of the installed basis: 0 none, 1 LR (Sec. 5.3), 2 Schur
+ * (Sec. 5.2); EINVAL for a NULL handle. */
+int ovs_deflate_scheme(ovs_gauge_t g);
+
+/* Save / restore an LR deflation basis to a binary file (header with dims,
  * mu, m_w, m and a checksum, then lambda, R, L in complex128). Restore
- * checks that dims, mu and m_w match the handle. Errors: EIO, ESTATE. */
+ * checks that dims, mu and m_w match the handle. Errors: EIO, ESTATE (also:
+ * a Schur basis, which is rebuilt from its right vectors instead). */
 int ovs_deflate_save(ovs_gauge_t g, const char* path);
 int ovs_deflate_restore(ovs_gauge_t g, const char* path);
 
@@ -179,9 +206,16 @@ typedef struct {
                             (zero-padded) is below tol; V is orthonormal,
                             so this is the change of its Krylov part */
     int32_t prec;        /* OVS_F64 or OVS_MIXED */
-    int32_t reserved;    /* must be 0 */
+    int32_t flags;       /* 0 or OVS_APPLY_HARMONIC (other bits: EINVAL) */
     double tol;          /* tolerance for check_every > 0 */
 } ovs_apply_opts;
+
+/* opts->flags: the harmonic variant of Sec. 4, which removes the even/odd
+ * see-saw of the error in k: sgn(H_k) is replaced by sgn(H^_k) with
+ * H^_k = H_k + |h_(k+1,k)|^2 H_k^-H e_k e_k^T (its eigenvalues are the
+ * harmonic Ritz values of H_w on the Krylov space); y = ... + beta V_k
+ * sgn(H^_k) e_1. Needs check_every = 0 and no Schur deflation. */
+#define OVS_APPLY_HARMONIC 1
 
 /* Per right-hand-side report. */
 typedef struct {
@@ -199,7 +233,12 @@ typedef struct {
  *   c = L^+ x, x_ominus = x - R c, y = R sgn(Re Lambda) c
  *     + beta V_k sgn(H_k) e_1 with the Arnoldi basis V_k of
  *   K_k(H_w, x_ominus), beta = ||x_ominus||; without a deflation basis the
- *   first three terms vanish (Sec. 4, Eq. yproj3).
+ *   first three terms vanish (Sec. 4, Eq. yproj3). With Schur deflation
+ *   (Sec. 5.2, Eq. formula): c = S^H x, x_perp = x - S c, V_k from the
+ *   modified Arnoldi recurrence that also orthogonalises against S
+ *   (Eq. modArnoldi), X = S^H H_w V_k, Y from T Y - Y H_k = sgn(T) X
+ *   - X sgn(H_k) by the row recurrences of App. A, and y = S (sgn(T) c
+ *   + beta Y e_1) + beta V_k sgn(H_k) e_1 (check_every must be 0).
  * Each right-hand side has its own Krylov basis; all are advanced together.
  * x: input [nrhs][N], y: output [nrhs][N] (complex128, host or device, must
  * not overlap). If info is not NULL the call waits for the stream and fills
@@ -211,6 +250,55 @@ typedef struct {
  * gave up; reported when the reports are read). */
 int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
                    ovs_apply_info* info, void* stream);
+
+/* y = D_ov(mu) x = x + gamma5 sgn(H_w(mu)) x for nrhs vectors (Sec. 2,
+ * Eq. Dov): ovs_sign_apply with the last step fused into the output layout
+ * pass. Arguments, reports and errors as ovs_sign_apply. */
+int ovs_overlap_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
+                      ovs_apply_info* info, void* stream);
+
+/* Options and per-right-hand-side report of the nested inversion. */
+typedef struct {
+    int32_t restart;    /* outer Krylov dimension per cycle, 1..256 */
+    int32_t max_cycles; /* restarts allowed, >= 1 */
+    double tol;         /* stop once ||b - D_ov x|| <= tol ||b|| */
+} ovs_solve_opts;
+
+typedef struct {
+    int32_t iters;      /* D_ov applications inside the cycles (all rhs advance together) */
+    int32_t cycles;     /* cycles run */
+    int32_t status;     /* OVS_OK, OVS_NOT_CONVERGED or OVS_ESIGN */
+    int32_t reserved;
+    double rel_resid;   /* ||b - D_ov x|| / ||b||, recomputed at the end of the last cycle */
+} ovs_solve_info;
+
+/* Solve D_ov(mu) x = b for nrhs right-hand sides by nested iteration: an
+ * outer restarted GMRES (zero initial guess, classical Gram-Schmidt applied
+ * twice, the least-squares problem updated by Givens rotations on the
+ * device) whose every iteration applies D_ov through the deflated Arnoldi
+ * method with `inner` and the installed deflation basis, which is set up
+ * once and reused by every application (the use of the method the paper
+ * names, Secs. 6 and 7; the outer method is not given there). All
+ * right-hand sides advance together; a cycle ends when every one has a
+ * least-squares residual below tol ||b|| (or the outer Krylov space became
+ * invariant), and the true residual b - D_ov x is recomputed at the end of
+ * each cycle. The host reads the residual estimates once per outer
+ * iteration. b, x: [nrhs][N] complex128, host or device. The outer basis
+ * ((restart + 1) nrhs N complex128) is allocated for the call and freed.
+ * info (if not NULL): nrhs reports. Returns OVS_OK when all converged,
+ * OVS_NOT_CONVERGED if some did not within max_cycles, or an error as
+ * ovs_sign_apply. */
+int ovs_overlap_solve(ovs_gauge_t g, const void* b, void* x, int32_t nrhs, const ovs_apply_opts* inner,
+                      const ovs_solve_opts* outer, ovs_solve_info* info, void* stream);
+
+/* Diagnosis and test hook (no counterpart in the paper): the Krylov basis
+ * and Hessenberg matrix of right-hand side `rhs` of the last application
+ * on this handle. *k_out = k_used; V (if not NULL): host complex128
+ * [k][N] canonical, v_1..v_k (converted from the basis precision); H (if
+ * not NULL): host complex128 column-major (k+1) x k, Hbar_k with
+ * h_(k+1,k) in its last row (after OVS_APPLY_HARMONIC its last column is
+ * the harmonic one). Synchronises the device. Errors: EINVAL. */
+int ovs_get_krylov(ovs_gauge_t g, int32_t rhs, int32_t* k_out, double* V, double* H);
 
 /* Batched form: n instances, each a handle with its own gauge field, mu and
  * deflation basis, and nrhs[i] right-hand sides x[i] -> y[i] (layout and

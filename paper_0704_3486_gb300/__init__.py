@@ -28,11 +28,15 @@ EXPORTS = [
     "ovs_create_gauge", "ovs_create_gauge_from_links", "ovs_get_links", "ovs_set_mu", "ovs_matvec",
     "ovs_matvec_noalloc",
     "ovs_deflate_setup", "ovs_deflate_stats", "ovs_set_setup_budget", "ovs_deflate_load", "ovs_deflate_get", "ovs_deflate_save", "ovs_deflate_restore",
+    "ovs_deflate_load_schur", "ovs_deflate_setup_schur", "ovs_deflate_scheme",
     "ovs_sign_apply", "ovs_sign_apply_batched", "ovs_get_info", "ovs_stencil_tuning", "ovs_set_stencil_shape",
+    "ovs_overlap_apply", "ovs_overlap_solve", "ovs_get_krylov",
     "ovs_profile_enable", "ovs_profile_read", "ovs_check_wait_timeout", "ovs_last_error", "ovs_version",
     "ovs_destroy",
 ]
 PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout", "proj"]
+APPLY_HARMONIC = 1
+SCHEME = {0: "none", 1: "lr", 2: "schur"}
 
 
 class OvsError(RuntimeError):
@@ -43,7 +47,19 @@ class OvsError(RuntimeError):
 
 class ApplyOpts(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("check_every", ctypes.c_int32), ("prec", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tol", ctypes.c_double)]
+                ("flags", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("cycles", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_resid", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "cycles": self.cycles, "status": self.status, "rel_resid": self.rel_resid}
 
 
 class ApplyInfo(ctypes.Structure):
@@ -84,6 +100,13 @@ def load(path=None):
         "ovs_deflate_get": ([vp, p_i32, vp, vp, vp], i32),
         "ovs_deflate_save": ([vp, ctypes.c_char_p], i32),
         "ovs_deflate_restore": ([vp, ctypes.c_char_p], i32),
+        "ovs_deflate_load_schur": ([vp, i32, vp], i32),
+        "ovs_deflate_setup_schur": ([vp, i32, dbl, vp], i32),
+        "ovs_deflate_scheme": ([vp], i32),
+        "ovs_overlap_apply": ([vp, vp, vp, i32, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp], i32),
+        "ovs_overlap_solve": ([vp, vp, vp, i32, ctypes.POINTER(ApplyOpts), ctypes.POINTER(SolveOpts),
+                               ctypes.POINTER(SolveInfo), vp], i32),
+        "ovs_get_krylov": ([vp, i32, p_i32, vp, vp], i32),
         "ovs_sign_apply": ([vp, vp, vp, i32, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp], i32),
         "ovs_sign_apply_batched": ([i32, vp, vp, vp, vp, ctypes.POINTER(ApplyOpts), ctypes.POINTER(ApplyInfo), vp],
                                    i32),
@@ -206,15 +229,30 @@ def matvec_noalloc(g, op, x, y, nrhs=None, prec=F64, stream=None):
                                      _stream(stream)))
 
 
-def deflate_setup(g, m, tol=1e-10, allow_unconverged=False):
-    """Returns (eigenvalues, status). With allow_unconverged, OVS_EEIG (basis
-    installed but not at tol) is returned as a status instead of raised."""
+def deflate_setup(g, m, tol=1e-10, allow_unconverged=False, scheme="lr"):
+    """Returns (eigenvalues, status). scheme "lr" (left and right vectors,
+    Sec. 5.3) or "schur" (right vectors only, Sec. 5.2). With
+    allow_unconverged, OVS_EEIG (basis installed but not at tol) is returned
+    as a status instead of raised."""
     import numpy as np
     eig = np.empty(2 * m, dtype=np.float64)
-    status = load().ovs_deflate_setup(g.handle, int(m), float(tol), _ptr(eig))
+    fn = load().ovs_deflate_setup_schur if scheme == "schur" else load().ovs_deflate_setup
+    status = fn(g.handle, int(m), float(tol), _ptr(eig))
     if not (allow_unconverged and status == -5):
         _check(status)
     return eig[0::2] + 1j * eig[1::2], status
+
+
+def deflate_load_schur(g, R):
+    """Schur deflation from right eigenvectors R: complex128 [m][N] (host)."""
+    import numpy as np
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.complex128))
+    m = R.shape[0]
+    _check(load().ovs_deflate_load_schur(g.handle, int(m), _ptr(R) if m else None))
+
+
+def deflate_scheme(g):
+    return SCHEME[_check(load().ovs_deflate_scheme(g.handle))]
 
 
 def deflate_stats(g):
@@ -246,16 +284,18 @@ def deflate_load(g, R, L, lam):
 
 
 def deflate_get(g):
+    """(R, L, lambda); for Schur deflation R holds S_m and L is None."""
     import numpy as np
     m = ctypes.c_int32()
     lib = load()
     _check(lib.ovs_deflate_get(g.handle, ctypes.byref(m), None, None, None))
     m = m.value
+    schur = lib.ovs_deflate_scheme(g.handle) == 2
     R = np.empty((m, g.N), dtype=np.complex128)
-    L = np.empty((m, g.N), dtype=np.complex128)
+    L = None if schur else np.empty((m, g.N), dtype=np.complex128)
     lam = np.empty(2 * m, dtype=np.float64)
     if m:
-        _check(lib.ovs_deflate_get(g.handle, None, _ptr(R), _ptr(L), _ptr(lam)))
+        _check(lib.ovs_deflate_get(g.handle, None, _ptr(R), None if schur else _ptr(L), _ptr(lam)))
     return R, L, lam[0::2] + 1j * lam[1::2]
 
 
@@ -267,18 +307,54 @@ def deflate_restore(g, path):
     _check(load().ovs_deflate_restore(g.handle, os.fsencode(path)))
 
 
-def sign_apply(g, x, y, k_max, prec=MIXED, nrhs=None, check_every=0, tol=0.0, stream=None, want_info=True):
-    """y = sgn(H_w(mu)) x. Returns (status, [info dicts]) if want_info, else status."""
+def _apply(fn, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info, harmonic):
     nrhs = x.shape[0] if nrhs is None else nrhs
-    opts = ApplyOpts(int(k_max), int(check_every), int(prec), 0, float(tol))
-    lib = load()
+    opts = ApplyOpts(int(k_max), int(check_every), int(prec), APPLY_HARMONIC if harmonic else 0, float(tol))
     if want_info:
         info = (ApplyInfo * nrhs)()
-        st = _check(lib.ovs_sign_apply(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), info,
-                                       _stream(stream)))
+        st = _check(fn(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), info, _stream(stream)))
         return st, [i.as_dict() for i in info]
-    return _check(lib.ovs_sign_apply(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), None,
-                                     _stream(stream)))
+    return _check(fn(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), None, _stream(stream)))
+
+
+def sign_apply(g, x, y, k_max, prec=MIXED, nrhs=None, check_every=0, tol=0.0, stream=None, want_info=True,
+               harmonic=False):
+    """y = sgn(H_w(mu)) x. Returns (status, [info dicts]) if want_info, else status."""
+    return _apply(load().ovs_sign_apply, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info, harmonic)
+
+
+def overlap_apply(g, x, y, k_max, prec=MIXED, nrhs=None, check_every=0, tol=0.0, stream=None, want_info=True,
+                  harmonic=False):
+    """y = D_ov(mu) x = x + gamma5 sgn(H_w(mu)) x (Sec. 2, Eq. Dov)."""
+    return _apply(load().ovs_overlap_apply, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info,
+                  harmonic)
+
+
+def overlap_solve(g, b, x, k_max, restart, tol, max_cycles=50, prec=MIXED, nrhs=None, harmonic=False, stream=None):
+    """Solve D_ov(mu) x = b by restarted GMRES around the sign application.
+    Returns (status, [info dicts: iters, cycles, status, rel_resid])."""
+    nrhs = b.shape[0] if nrhs is None else nrhs
+    inner = ApplyOpts(int(k_max), 0, int(prec), APPLY_HARMONIC if harmonic else 0, 0.0)
+    outer = SolveOpts(int(restart), int(max_cycles), float(tol))
+    info = (SolveInfo * nrhs)()
+    st = _check(load().ovs_overlap_solve(g.handle, _ptr(b), _ptr(x), int(nrhs), ctypes.byref(inner),
+                                         ctypes.byref(outer), info, _stream(stream)))
+    return st, [i.as_dict() for i in info]
+
+
+def get_krylov(g, rhs):
+    """(V [k][N] complex128, Hbar [(k+1) x k] complex128) of right-hand side
+    rhs of the last application (a test and diagnosis hook)."""
+    import numpy as np
+    lib = load()
+    k = ctypes.c_int32()
+    _check(lib.ovs_get_krylov(g.handle, int(rhs), ctypes.byref(k), None, None))
+    k = k.value
+    V = np.empty((k, g.N), dtype=np.complex128)
+    H = np.empty((k, k + 1), dtype=np.complex128)  # column-major (k+1) x k
+    if k:
+        _check(lib.ovs_get_krylov(g.handle, int(rhs), ctypes.byref(ctypes.c_int32()), _ptr(V), _ptr(H)))
+    return V, H.T.copy()
 
 
 def sign_apply_batched(gauges, xs, ys, k_max, prec=MIXED, check_every=0, tol=0.0, stream=None, want_info=True):

@@ -25,7 +25,7 @@
 
 namespace ovs {
 void generate_links(long long V, uint64_t seed, double eps, double* links);
-int eig_setup(struct ovs_gauge_s* g, int m, double tol, double* eig_out);
+int eig_setup(struct ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur);
 }  // namespace ovs
 
 using namespace ovs;
@@ -234,7 +234,10 @@ static void free_kry(KryWork& k) {
     dfree(k.newton);
     dfree(k.cdef);
     dfree(k.cdef2);
-    k.nrhs = k.kmax = k.jcap = k.nblk = 0;
+    dfree(k.X);
+    dfree(k.sylv);
+    dfree(k.cS);
+    k.nrhs = k.kmax = k.jcap = k.nblk = k.mdef = 0;
     k.prec = -1;
 }
 
@@ -244,14 +247,17 @@ static void drop_graphs(ovs_gauge_s* g) {
     ++g->gen;
 }
 
-static void free_deflation(ovs_gauge_s* g) {
+void ovs::free_deflation(ovs_gauge_s* g) {
     drop_graphs(g);
     dfree(g->R64);
     dfree(g->L64);
     dfree(g->R32);
     dfree(g->L32);
     dfree(g->sgn);
+    dfree(g->schurT);
+    dfree(g->schurFT);
     g->m = 0;
+    g->scheme = DEFL_NONE;
     g->lambda.clear();
 }
 
@@ -280,7 +286,10 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     const int nblk_need =
         std::max(std::max(plan.nblk, plan1.nblk),
                  tprec == PREC_F32 ? gdots_chunk_slots(field_units(g->N, tprec), nrhs, g->num_sms) : 0);
-    if (k.prec == tprec && k.nrhs >= nrhs && k.kmax >= kmax && k.jcap >= jneed && k.nblk >= nblk_need) return OVS_OK;
+    const bool schur = g->scheme == DEFL_SCHUR;
+    if (k.prec == tprec && k.nrhs >= nrhs && k.kmax >= kmax && k.jcap >= jneed && k.nblk >= nblk_need &&
+        k.mdef >= g->m && (!schur || k.X != nullptr))
+        return OVS_OK;
     const bool same = (k.prec == tprec);
     const int n = std::max(nrhs, same ? k.nrhs : 0);
     const int km = std::max(kmax, same ? k.kmax : 0);
@@ -309,8 +318,15 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     CK(dalloc(&k.status, sizeof(int) * n));
     CK(dalloc(&k.coeff, sizeof(double2) * (size_t)km * n));
     CK(dalloc(&k.newton, sizeof(double2) * 2 * (size_t)km * km * n));
-    CK(dalloc(&k.cdef, sizeof(double2) * (size_t)std::max(g->m, 1) * n));
-    CK(dalloc(&k.cdef2, sizeof(double2) * (size_t)std::max(g->m, 1) * n));
+    const int md = std::max(std::max(g->m, 1), same ? k.mdef : 0);
+    CK(dalloc(&k.cdef, sizeof(double2) * (size_t)md * n));
+    CK(dalloc(&k.cdef2, sizeof(double2) * (size_t)md * n));
+    if (schur) {
+        CK(dalloc(&k.X, sizeof(double2) * (size_t)md * km * n));
+        CK(dalloc(&k.sylv, sizeof(double2) * (size_t)schur_scratch_per_rhs(md) * n));
+        CK(dalloc(&k.cS, sizeof(double2) * (size_t)md * n));
+    }
+    k.mdef = md;
     k.nrhs = n;
     k.kmax = km;
     k.jcap = jc;
@@ -560,6 +576,7 @@ int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, con
     }
     cudaFree(Ltmp);
     g->m = m;
+    g->scheme = DEFL_LR;
     g->lambda.assign(lambda, lambda + 2 * m);
     return OVS_OK;
 }
@@ -590,8 +607,33 @@ int ovs_deflate_load(ovs_gauge_t g, int32_t m, const double* R, const double* L,
     return rc;
 }
 
+int ovs_deflate_load_schur(ovs_gauge_t g, int32_t m, const double* R) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
+    if (m < 0 || (long long)m > g->N) return fail(OVS_EINVAL, "m out of range");
+    if (m > 0 && !R) return fail(OVS_EINVAL, "NULL R");
+    if (m == 0) {
+        free_deflation(g);
+        return OVS_OK;
+    }
+    const size_t f64 = field_bytes(g->N, PREC_F64);
+    void* Rd = nullptr;
+    CK(dalloc(&Rd, f64 * m));
+    const cudaError_t e = cudaMemcpy(Rd, R, f64 * m, cudaMemcpyHostToDevice);
+    int rc = e == cudaSuccess ? install_schur(g, m, Rd) : fail(OVS_ECUDA, "deflate_load_schur upload: %s",
+                                                              cudaGetErrorString(e));
+    cudaFree(Rd);
+    return rc;
+}
+
+int ovs_deflate_scheme(ovs_gauge_t g) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    return g->scheme;
+}
+
 int ovs_deflate_get(ovs_gauge_t g, int32_t* m_out, double* R, double* L, double* lambda) {
     if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (L && g->scheme == DEFL_SCHUR) return fail(OVS_ESTATE, "Schur deflation keeps no left vectors");
     if (m_out) *m_out = g->m;
     const int m = g->m;
     if (m == 0) return OVS_OK;
@@ -632,6 +674,7 @@ struct DeflHeader {
 int ovs_deflate_save(ovs_gauge_t g, const char* path) {
     if (!g || !path) return fail(OVS_EINVAL, "NULL argument");
     if (g->m == 0) return fail(OVS_ESTATE, "no deflation basis installed");
+    if (g->scheme != DEFL_LR) return fail(OVS_ESTATE, "only an LR deflation basis can be saved");
     const int m = g->m;
     const size_t f64 = field_bytes(g->N, PREC_F64);
     std::vector<double> R((size_t)m * g->N * 2), L((size_t)m * g->N * 2), lam(2 * m);
@@ -714,7 +757,15 @@ int ovs_deflate_setup(ovs_gauge_t g, int32_t m, double tol, double* eig_out) {
     if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
     if (m <= 0 || (long long)m * 4 > g->N) return fail(OVS_EINVAL, "m must be in [1, N/4]");
     if (!(tol > 0.0)) return fail(OVS_EINVAL, "tol must be > 0");
-    return eig_setup(g, m, tol, eig_out);
+    return eig_setup(g, m, tol, eig_out, false);
+}
+
+int ovs_deflate_setup_schur(ovs_gauge_t g, int32_t m, double tol, double* eig_out) {
+    if (!g) return fail(OVS_EINVAL, "NULL handle");
+    if (!g->mu_set) return fail(OVS_ESTATE, "call ovs_set_mu first");
+    if (m <= 0 || (long long)m * 4 > g->N) return fail(OVS_EINVAL, "m must be in [1, N/4]");
+    if (!(tol > 0.0)) return fail(OVS_EINVAL, "tol must be > 0");
+    return eig_setup(g, m, tol, eig_out, true);
 }
 
 // ---------------------------------------------------------- sign apply
@@ -734,6 +785,12 @@ static int check_apply(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts) {
     const int every = opts->check_every;
     if (every < 0 || (every % 2) != 0) return fail(OVS_EINVAL, "check_every must be 0 or a positive even number");
     if (every > 0 && !(opts->tol > 0.0)) return fail(OVS_EINVAL, "check_every > 0 needs tol > 0");
+    if ((opts->flags & ~OVS_APPLY_HARMONIC) != 0) return fail(OVS_EINVAL, "unknown bits in opts->flags");
+    const bool harmonic = (opts->flags & OVS_APPLY_HARMONIC) != 0;
+    if (harmonic && every > 0) return fail(OVS_EINVAL, "OVS_APPLY_HARMONIC needs check_every = 0");
+    if (g->scheme == DEFL_SCHUR && (every > 0 || harmonic))
+        return fail(OVS_EINVAL, "Schur deflation supports fixed-k applications without OVS_APPLY_HARMONIC");
+    if (g->scheme == DEFL_SCHUR && !schur_coeff_fits(k)) return fail(OVS_EINVAL, "k_max too large for Schur deflation");
     return OVS_OK;
 }
 
@@ -745,7 +802,7 @@ static int check_apply(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts) {
 // batched form tunes before it records), so the sequence can be recorded as
 // a CUDA graph.
 static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, const ovs_apply_opts* opts,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool overlap = false) {
     const int k = opts->k_max;
     const int every = opts->check_every;
     const int tp = tprec_of(opts->prec);
@@ -768,9 +825,46 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
     KL(OVS_PROF_LAYOUT, bytes_layout(N, tp, nrhs), launch_to_internal(tp, xd, N, w.xint, fb, V, nrhs, st));
     CK(cudaMemsetAsync(kw.H, 0, sizeof(double2) * h_rhs * nrhs, st));
 
-    // K5: LR projection (Sec. 5.3 step iii) and the exact deflated part
+    // K5: LR projection (Sec. 5.3 step iii) and the exact deflated part, or
+    // the Schur projection (Sec. 5.2 step iii)
     const int m = g->m;
-    if (m > 0) {
+    const bool schur = m > 0 && g->scheme == DEFL_SCHUR;
+    const void* Sb = tp == PREC_F64 ? g->R64 : g->R32;  // Schur vectors (schur)
+    const int S1 = gdots_stride(1, std::max(m, 1));
+    const long long x_rhs = (long long)kw.mdef * kmax;  // Schur: X = S^H H_w V_k per right-hand side
+    // v_r -= S coef_r (the Schur vectors shared by all right-hand sides)
+    auto schur_out = [&](const void* coef, long long coef_stride, void* v) -> int {
+        if (tp == PREC_F32 && m <= 1536)
+            KL(OVS_PROF_PROJ, bytes_update(N, tp, tp, m, nrhs, true, true),
+               launch_shared_combine(PREC_F32, Sb, units, m, coef, coef_stride, -1.0, v, N, v, N, units, nrhs, st));
+        else
+            KL(OVS_PROF_PROJ, bytes_update(N, tp, tp, m, nrhs, true, true),
+               launch_update(tp, tp, Sb, 0, units, m, nullptr, coef, coef_stride, -1.0, v, N, v, N, units, plan, nrhs,
+                             nullptr, nullptr, st));
+        return OVS_OK;
+    };
+    // partial sums of S^H v_r (reduced by the caller)
+    auto schur_dots = [&](const void* v) -> int {
+        KL(OVS_PROF_PROJ, bytes_dots(N, tp, m, nrhs, true),
+           launch_gdots(tp, 1, Sb, 0, units, m, v, units, nullptr, 0, false, units, plan, nrhs, kw.partial, kw.active,
+                        st));
+        return OVS_OK;
+    };
+    if (schur) {
+        // c = S^H x, x_perp = x - S c, classical Gram-Schmidt applied twice
+        CK(cudaMemsetAsync(kw.active, 0xff, sizeof(int) * nrhs, st));
+        TRY(schur_dots(w.xint));
+        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
+           launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef, m, false, nullptr, st));
+        TRY(schur_out(kw.cdef, m, w.xint));
+        TRY(schur_dots(w.xint));
+        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
+           launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef2, m, false, nullptr, st));
+        TRY(schur_out(kw.cdef2, m, w.xint));
+        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
+           launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef, m, true, nullptr, st));
+        CK(cudaMemsetAsync(w.yacc, 0, f64 * nrhs, st));
+    } else if (m > 0) {
         const void* Lb = tp == PREC_F64 ? g->L64 : g->L32;
         const void* Rb = tp == PREC_F64 ? g->R64 : g->R32;
         const int S = gdots_stride(1, m);
@@ -822,6 +916,21 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         KL(OVS_PROF_MATVEC, bw,
            launch_wilson(tp, true, links_for(g, tp), w.xint, fb, w.wvec, fb, g->geom, nrhs, g->kappa, g->mu,
                          kw.active, st, sh));
+        if (schur) {
+            // modified Arnoldi (Eq. modArnoldi): z <- z - S (S^H z), twice;
+            // xz = S^H z (both passes) lands in column j of X
+            char* Xj = (char*)kw.X + sizeof(double2) * (size_t)j * m;
+            TRY(schur_dots(w.wvec));
+            KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
+               launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, Xj, x_rhs, false, kw.active, st));
+            TRY(schur_out(Xj, x_rhs, w.wvec));
+            TRY(schur_dots(w.wvec));
+            KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
+               launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef2, m, false, kw.active, st));
+            TRY(schur_out(kw.cdef2, m, w.wvec));
+            KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
+               launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, Xj, x_rhs, true, kw.active, st));
+        }
         const bool tma = (tp == PREC_F32) && tma_update_fits(j);
         const bool chunked = (tp == PREC_F32) && gdots_chunk_fits(j);
         const int dblk = chunked ? dslots : plan.nblk;
@@ -838,6 +947,9 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         KL(OVS_PROF_SMALL, 16.0 * 3.0 * j * nrhs,
            launch_arnoldi_step(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.beta, kw.inv_beta, kw.dcoef, kw.hnorm2,
                                kw.active, kw.k_used, nrhs, st));
+        if (schur)  // X[:, j] = (xz - X[:, <j] s) / beta_j
+            KL(OVS_PROF_SMALL, 16.0 * ((double)m * j + 2.0 * m) * nrhs,
+               launch_schur_xcol(kw.X, x_rhs, m, j, kw.htmp, kw.jcap, kw.inv_beta, kw.active, nrhs, st));
         KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 2.0 * j) * nrhs,
            launch_arnoldi_column(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.inv_beta, kw.dcoef, kw.active, nrhs, st));
         // A7 (batched form): every `every` steps, the sign of the complete
@@ -882,10 +994,32 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         KL(OVS_PROF_SMALL, 16.0 * 2.0 * k * nrhs,
            launch_arnoldi_final(kw.htmp, kw.jcap, k, k, kw.H, h_rhs, ldh, kw.active, nrhs, st));
     }
-    // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v)
+    // harmonic variant (Sec. 4): H_k -> H_k + |h_(k+1,k)|^2 H_k^-H e_k e_k^T
+    if (opts->flags & OVS_APPLY_HARMONIC)
+        KL(OVS_PROF_SMALL, 16.0 * (double)k * (k + 1) * nrhs,
+           launch_harmonic(kw.H, h_rhs, ldh, kw.k_used, kw.newton, (int)kmax, nrhs, st));
+    // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v; Sec. 5.2 step v for H_k)
     KL(OVS_PROF_NEWTON, 16.0 * (double)k * k * nrhs,
        launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.coeff, kmax, kw.newton, (int)kmax, nrhs, kw.iters,
                      kw.status, st));
+    if (schur) {
+        // Schur coefficients sgn(T) c + beta Y e_1 (App. A), then y = S cS
+        KL(OVS_PROF_SMALL, 16.0 * ((double)m * k * 4 + (double)k * k) * nrhs,
+           launch_schur_coeff(g->schurT, g->schurFT, m, kw.X, x_rhs, kw.H, h_rhs, ldh, kw.newton, 2 * kmax * kmax,
+                              kw.k_used, kw.status, kw.beta, kw.cdef, m, kw.sylv, kw.cS, m, nrhs, st));
+        if (tp == PREC_F64)
+            KL(OVS_PROF_PROJ, bytes_update(N, PREC_F64, PREC_F64, m, nrhs, true, false),
+               launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cS, m, 1.0, nullptr, 0, w.yacc, N, N,
+                             plan64, nrhs, nullptr, nullptr, st));
+        else if (m <= 1536)
+            KL(OVS_PROF_PROJ, bytes_update(N, PREC_F32, PREC_F64, m, nrhs, true, false),
+               launch_shared_combine(PREC_F64, g->R32, units, m, kw.cS, m, 1.0, nullptr, 0, w.yacc, N, units, nrhs,
+                                     st));
+        else
+            KL(OVS_PROF_PROJ, bytes_update(N, PREC_F32, PREC_F64, m, nrhs, true, false),
+               launch_update(PREC_F32, PREC_F64, g->R32, 0, units, m, nullptr, kw.cS, m, 1.0, nullptr, 0, w.yacc,
+                             N, units, plan, nrhs, nullptr, nullptr, st));
+    }
     // K4: y += V_k c (Sec. 5.3 step vi)
     if (tp == PREC_F32 && recombine_tma_fits(k))
         KL(OVS_PROF_PROJ, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
@@ -895,8 +1029,12 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         KL(OVS_PROF_PROJ, bytes_update(N, tp, PREC_F64, k, nrhs, false, true),
            launch_update(tp, PREC_F64, basis, basis_rhs_units, units, k, kw.k_used, kw.coeff, kmax, 1.0, w.yacc, N,
                          w.yacc, N, units, plan, nrhs, nullptr, nullptr, st));
-    KL(OVS_PROF_LAYOUT, bytes_layout(N, PREC_F64, nrhs), launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
-    (void)f64;
+    if (overlap)  // D_ov(mu) x = x + gamma5 sgn(H_w) x (Sec. 2, Eq. Dov), fused into the layout pass
+        KL(OVS_PROF_LAYOUT, bytes_layout(N, PREC_F64, nrhs) + 16.0 * N * nrhs,
+           launch_to_canonical_overlap(w.yacc, f64, xd, N, yd, N, V, nrhs, st));
+    else
+        KL(OVS_PROF_LAYOUT, bytes_layout(N, PREC_F64, nrhs),
+           launch_to_canonical(PREC_F64, w.yacc, f64, yd, N, V, nrhs, st));
     return OVS_OK;
 }
 
@@ -910,8 +1048,11 @@ static void remember_apply(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts,
 
 extern "C" {
 
-int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
-                   ovs_apply_info* info, void* stream) {
+}  // extern "C"
+
+// ovs_sign_apply (overlap = false) and ovs_overlap_apply (overlap = true)
+static int apply_entry(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
+                       ovs_apply_info* info, void* stream, bool overlap) {
     if (!x || !y) return fail(OVS_EINVAL, "NULL argument");
     TRY(check_apply(g, nrhs, opts));
     cudaStream_t st = (cudaStream_t)stream;
@@ -926,11 +1067,184 @@ int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ov
         xd = g->vw.sx;
     }
     void* yd = ydev ? y : g->vw.sy;
-    TRY(sign_apply_core(g, xd, yd, nrhs, opts, st));
+    TRY(sign_apply_core(g, xd, yd, nrhs, opts, st, overlap));
     if (!ydev) CK(cudaMemcpyAsync(y, yd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
     remember_apply(g, nrhs, opts, st);
     if (info) return ovs_get_info(g, info, nrhs);
     if (!ydev) CK(cudaStreamSynchronize(st));
+    return OVS_OK;
+}
+
+extern "C" {
+
+int ovs_sign_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
+                   ovs_apply_info* info, void* stream) {
+    return apply_entry(g, x, y, nrhs, opts, info, stream, false);
+}
+
+int ovs_overlap_apply(ovs_gauge_t g, const void* x, void* y, int32_t nrhs, const ovs_apply_opts* opts,
+                      ovs_apply_info* info, void* stream) {
+    return apply_entry(g, x, y, nrhs, opts, info, stream, true);
+}
+
+int ovs_overlap_solve(ovs_gauge_t g, const void* b, void* x, int32_t nrhs, const ovs_apply_opts* inner,
+                      const ovs_solve_opts* outer, ovs_solve_info* info, void* stream) {
+    if (!b || !x || !outer) return fail(OVS_EINVAL, "NULL argument");
+    TRY(check_apply(g, nrhs, inner));
+    const int restart = outer->restart;
+    if (restart < 1 || restart > 256) return fail(OVS_EINVAL, "restart must be in [1, 256]");
+    if (outer->max_cycles < 1) return fail(OVS_EINVAL, "max_cycles must be >= 1");
+    if (!(outer->tol > 0.0)) return fail(OVS_EINVAL, "tol must be > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tp = tprec_of(inner->prec);
+    TRY(ensure_vec(g, nrhs, tp));
+    TRY(ensure_kry(g, nrhs, inner->k_max, tp));
+    const long long N = g->N;
+    const size_t f64 = field_bytes(N, PREC_F64);
+    const int jc = gdots_stride(1, restart + 1);
+    const BlasPlan plan = blas_plan(N, nrhs, g->num_sms);
+    const int nb = norm_blocks();
+    // work space of the outer iteration, owned by this call
+    struct Bufs {
+        std::vector<void*> p;
+        ~Bufs() {
+            for (void* q : p)
+                if (q) cudaFree(q);
+        }
+        void* get(size_t bytes) {  // nullptr (recorded) when the allocation fails
+            void* q = nullptr;
+            if (cudaMalloc(&q, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                q = nullptr;
+            }
+            p.push_back(q);
+            return q;
+        }
+    } bufs;
+    void* W = bufs.get(f64 * (size_t)(restart + 1) * nrhs);
+    void* z = bufs.get(f64 * nrhs);
+    void* r = bufs.get(f64 * nrhs);
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    void* bd = bdev ? const_cast<void*>(b) : bufs.get(f64 * nrhs);
+    void* xd = xdev ? x : bufs.get(f64 * nrhs);
+    void* red1 = bufs.get(sizeof(double2) * (size_t)jc * nrhs);
+    void* red2 = bufs.get(sizeof(double2) * (size_t)jc * nrhs);
+    void* part = bufs.get(sizeof(double2) * (size_t)plan.nblk * jc * nrhs);
+    double* npart = (double*)bufs.get(sizeof(double) * (size_t)nb * nrhs);
+    void* R = bufs.get(sizeof(double2) * (size_t)restart * restart * nrhs);
+    void* rot = bufs.get(sizeof(double2) * 2 * (size_t)restart * nrhs);
+    void* gv = bufs.get(sizeof(double2) * (size_t)(restart + 1) * nrhs);
+    void* yv = bufs.get(sizeof(double2) * (size_t)restart * nrhs);
+    double* sc = (double*)bufs.get(sizeof(double) * 5 * (size_t)nrhs);  // beta, 1/beta, est, 1/h, |r|
+    for (void* q : bufs.p)
+        if (!q) return fail(OVS_ENOMEM, "overlap_solve: device memory for the outer basis");
+    double *beta = sc, *inv_beta = sc + nrhs, *est = sc + 2 * nrhs, *inv_hn = sc + 3 * nrhs, *rn = sc + 4 * nrhs;
+    if (!bdev) CK(cudaMemcpyAsync(bd, b, f64 * nrhs, cudaMemcpyHostToDevice, st));
+    std::vector<double> bnorm(nrhs), h_est(nrhs), h_ih(nrhs), h_rn(nrhs);
+    CK(launch_norms(bd, N, N, nrhs, npart, rn, nullptr, st));
+    CK(cudaMemcpyAsync(bnorm.data(), rn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemsetAsync(xd, 0, f64 * nrhs, st));
+    CK(cudaMemcpyAsync(r, bd, f64 * nrhs, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    int iters = 0, cycles = 0;
+    bool converged = false;
+    for (int cyc = 1; cyc <= outer->max_cycles && !converged; ++cyc) {
+        // w_0 = r / ||r||, g = ||r|| e_1
+        CK(launch_norms(r, N, N, nrhs, npart, beta, inv_beta, st));
+        CK(launch_scale(r, N, W, N, inv_beta, N, nrhs, st));
+        CK(launch_gmres_start(beta, gv, restart, nrhs, st));
+        int jj = 0;
+        for (int j = 0; j < restart; ++j) {
+            char* Wj = (char*)W + f64 * (size_t)j * nrhs;
+            TRY(sign_apply_core(g, Wj, z, nrhs, inner, st, true));  // z = D_ov w_j
+            ++iters;
+            for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+                void* red = pass ? red2 : red1;
+                CK(launch_gdots(PREC_F64, 1, W, N, (long long)nrhs * N, j + 1, z, N, nullptr, 0, false, N, plan, nrhs,
+                                part, nullptr, st));
+                CK(launch_reduce(part, plan.nblk, gdots_stride(1, j + 1), j + 1, nrhs, red, jc, false, nullptr, st));
+                CK(launch_update(PREC_F64, PREC_F64, W, N, (long long)nrhs * N, j + 1, nullptr, red, jc, -1.0, z, N, z,
+                                 N, N, plan, nrhs, nullptr, nullptr, st));
+            }
+            CK(launch_norm_partials(z, N, N, nrhs, npart, st));
+            CK(launch_gmres_col(red1, red2, jc, npart, j, restart, R, rot, gv, est, inv_hn, nrhs, st));
+            jj = j + 1;
+            if (j + 1 < restart) CK(launch_scale(z, N, (char*)W + f64 * (size_t)(j + 1) * nrhs, N, inv_hn, N, nrhs, st));
+            CK(cudaMemcpyAsync(h_est.data(), est, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(h_ih.data(), inv_hn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            bool all = true, breakdown = false;
+            for (int q = 0; q < nrhs; ++q) {
+                all = all && !(h_est[q] > outer->tol * bnorm[q]);
+                breakdown = breakdown || h_ih[q] == 0.0;
+            }
+            if (all || breakdown) break;
+        }
+        // x += W y with y = R^-1 g; true residual r = b - D_ov x
+        CK(launch_gmres_backsub(R, gv, jj, restart, yv, nrhs, st));
+        CK(launch_update(PREC_F64, PREC_F64, W, N, (long long)nrhs * N, jj, nullptr, yv, restart, 1.0, xd, N, xd, N, N,
+                         plan, nrhs, nullptr, nullptr, st));
+        TRY(sign_apply_core(g, xd, z, nrhs, inner, st, true));
+        CK(launch_sub(bd, z, r, N, nrhs, st));
+        CK(launch_norms(r, N, N, nrhs, npart, rn, nullptr, st));
+        CK(cudaMemcpyAsync(h_rn.data(), rn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        cycles = cyc;
+        converged = true;
+        for (int q = 0; q < nrhs; ++q) converged = converged && !(h_rn[q] > outer->tol * bnorm[q]);
+    }
+    if (!xdev) CK(cudaMemcpyAsync(x, xd, f64 * nrhs, cudaMemcpyDeviceToHost, st));
+    remember_apply(g, nrhs, inner, st);
+    // reports of the last inner application: timeouts and sign failures
+    std::vector<ovs_apply_info> ii(nrhs);
+    const int inner_rc = ovs_get_info(g, ii.data(), nrhs);
+    if (inner_rc < 0) return inner_rc;
+    int worst = OVS_OK;
+    for (int q = 0; q < nrhs; ++q) {
+        const double rel = bnorm[q] > 0.0 ? h_rn[q] / bnorm[q] : 0.0;
+        const bool ok = !(h_rn[q] > outer->tol * bnorm[q]);
+        int stq = ok ? OVS_OK : OVS_NOT_CONVERGED;
+        if (ii[q].status == OVS_ESIGN) stq = OVS_ESIGN;
+        if (stq == OVS_ESIGN) worst = OVS_ESIGN;
+        else if (stq == OVS_NOT_CONVERGED && worst == OVS_OK) worst = OVS_NOT_CONVERGED;
+        if (info) {
+            info[q].iters = iters;
+            info[q].cycles = cycles;
+            info[q].status = stq;
+            info[q].reserved = 0;
+            info[q].rel_resid = rel;
+        }
+    }
+    return worst;
+}
+
+int ovs_get_krylov(ovs_gauge_t g, int32_t rhs, int32_t* k_out, double* V, double* H) {
+    if (!g || !k_out) return fail(OVS_EINVAL, "NULL argument");
+    if (rhs < 0 || rhs >= g->last_nrhs) return fail(OVS_EINVAL, "rhs outside the last application");
+    KryWork& kw = g->kw;
+    CK(cudaStreamSynchronize(g->last_stream));
+    int k = 0;
+    CK(cudaMemcpy(&k, kw.k_used + rhs, sizeof(int), cudaMemcpyDeviceToHost));
+    *k_out = k;
+    if (k <= 0) return OVS_OK;
+    const long long N = g->N;
+    const int tp = kw.prec;
+    const size_t fb = field_bytes(N, tp), f64 = field_bytes(N, PREC_F64);
+    if (V) {
+        void* tmp = nullptr;
+        CK(dalloc(&tmp, f64 * k));
+        const char* b = (const char*)kw.basis + fb * (size_t)(kw.kmax + 1) * rhs;
+        cudaError_t e = launch_to_canonical(tp, b, fb, tmp, N, (int)g->V, k, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(V, tmp, f64 * k, cudaMemcpyDeviceToHost);
+        cudaFree(tmp);
+        CK(e);
+    }
+    if (H) {
+        const int ldh = kw.kmax + 1;
+        const double2* Hr = (const double2*)kw.H + (size_t)(kw.kmax + 1) * kw.kmax * rhs;
+        CK(cudaMemcpy2D(H, sizeof(double2) * (k + 1), Hr, sizeof(double2) * ldh, sizeof(double2) * (k + 1), k,
+                        cudaMemcpyDeviceToHost));
+    }
     return OVS_OK;
 }
 

@@ -364,6 +364,28 @@ __global__ void k_to_canonical(const char* __restrict__ in, size_t in_stride, do
     for (int q = 0; q < 12; ++q) dst[q] = make_double2(double(p[q].re), double(p[q].im));
 }
 
+// D_ov(mu) y = x + gamma5 sgn(H_w) x (Sec. 2, Eq. Dov) fused into the last
+// layout pass: in holds sgn(H_w) x in internal complex128 planes, x is the
+// canonical source; gamma5 = diag(1, 1, -1, -1) flips the entries of spin
+// 2 and 3 (spin*3 + colour >= 6).
+__global__ void k_to_canonical_overlap(const char* __restrict__ in, size_t in_stride,
+                                       const double2* __restrict__ x, size_t x_stride, double2* __restrict__ canon,
+                                       size_t canon_stride, int V) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (s >= V) return;
+    cplx<double> p[12];
+    Field<double>::load(in + r * in_stride, V, s, p);
+    const double2* xs = x + r * x_stride + (size_t)s * 12;
+    double2* dst = canon + r * canon_stride + (size_t)s * 12;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        const double2 xv = xs[q];
+        const double g = q < 6 ? 1.0 : -1.0;
+        dst[q] = make_double2(fma(g, p[q].re, xv.x), fma(g, p[q].im, xv.y));
+    }
+}
+
 // canonical links complex128 [V][4][3][3] -> planes [nu][e][V] (complex128 and,
 // if u32 != nullptr, complex64)
 __global__ void k_links_to_internal(const double2* __restrict__ canon, double2* __restrict__ u64,
@@ -496,6 +518,14 @@ cudaError_t launch_to_canonical(int prec, const void* in, size_t in_stride, void
         k_to_canonical<double><<<grid, 128, 0, st>>>((const char*)in, in_stride, (double2*)canon, canon_stride_cplx, V);
     else
         k_to_canonical<float><<<grid, 128, 0, st>>>((const char*)in, in_stride, (double2*)canon, canon_stride_cplx, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_canonical_overlap(const void* in, size_t in_stride, const void* x, size_t x_stride_cplx,
+                                        void* canon, size_t canon_stride_cplx, int V, int nrhs, cudaStream_t st) {
+    dim3 grid = site_grid(V, nrhs, 128);
+    k_to_canonical_overlap<<<grid, 128, 0, st>>>((const char*)in, in_stride, (const double2*)x, x_stride_cplx,
+                                                 (double2*)canon, canon_stride_cplx, V);
     return cudaGetLastError();
 }
 

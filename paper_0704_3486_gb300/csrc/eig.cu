@@ -32,6 +32,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <numeric>
 #include <vector>
 
@@ -329,8 +330,16 @@ FilterPlan plan_filter(double b, double lm, double a, double kappa, double mu, d
     return fp;
 }
 
+// OVS_SETUP_LOG=1 in the environment prints one line per iteration of the
+// set-up to stderr (degree, precision, residuals, time): a diagnosis aid.
+bool setup_log() {
+    const char* v = std::getenv("OVS_SETUP_LOG");
+    return v != nullptr && v[0] == '1';
+}
+
 int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadline_s, SideResult& res) {
     const auto t_start = std::chrono::steady_clock::now();
+    const bool log = setup_log();
     const int p = c.p;
     const long long N = c.N;
     ovs_gauge_s* g = c.g;
@@ -385,6 +394,21 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
         double rmax = 0.0;
         for (int i = 0; i < m; ++i) rmax = std::max(rmax, res.resid[order[i]] / hnorm);
         res.iters = it + 1;
+        if (log) {
+            double rmed = 0.0;
+            std::vector<double> rr(m);
+            for (int i = 0; i < m; ++i) rr[i] = res.resid[order[i]] / hnorm;
+            std::sort(rr.begin(), rr.end());
+            rmed = rr[m / 2];
+            int nconv = 0;
+            for (int i = 0; i < m; ++i) nconv += rr[i] <= tol;
+            std::fprintf(stderr,
+                         "[setup] mu=%+.3f it=%d deg=%d prec=%s |theta| m-th=%.4e p-th=%.4e resid max=%.3e "
+                         "median=%.3e converged=%d/%d elapsed=%.2fs\n",
+                         mu, it + 1, fp.deg, fprec == PREC_F32 ? "c64" : "c128", std::abs(res.theta[order[m - 1]]),
+                         std::abs(res.theta[order[p - 1]]), rmax, rmed, nconv, m,
+                         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+        }
         if (rmax <= tol) {
             res.converged = true;
             break;
@@ -426,9 +450,63 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
     return OVS_OK;
 }
 
+// Schur deflation needs the right vectors only (Sec. 5.2 step i; Sec. 5.4):
+// the m converged pairs of smallest |Re lambda| (all m if fewer converged)
+// become the Schur basis, in that order.
+int finish_schur(Ctx& c, ovs_gauge_s* g, int m, double tol, const SideResult& right, double* eig_out) {
+    const int p = c.p;
+    const long long N = c.N;
+    std::vector<int> cand;
+    for (int i = 0; i < p; ++i)
+        if (right.resid[i] <= tol) cand.push_back(i);
+    bool ok = right.converged;
+    if ((int)cand.size() < m) {
+        cand.clear();
+        for (int i = 0; i < m; ++i) cand.push_back(i);
+        ok = false;
+    }
+    std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) {
+        return std::fabs(right.theta[x].real()) < std::fabs(right.theta[y].real());
+    });
+    cand.resize(m);
+    const size_t fv = sizeof(double2) * (size_t)N;
+    double2 *Rc = nullptr, *tmp = nullptr;
+    cudaError_t e = cudaMalloc((void**)&Rc, fv * m);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&tmp, fv * m);
+    for (int i = 0; i < m && e == cudaSuccess; ++i)
+        e = cudaMemcpy(tmp + (size_t)i * N, c.Q + (size_t)cand[i] * N, fv, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = launch_to_canonical(PREC_F64, tmp, fv, Rc, N, (int)g->V, m, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        if (Rc) cudaFree(Rc);
+        cudaGetLastError();
+        return lib_fail(OVS_ECUDA, "deflate_setup_schur: gathering eigenvectors failed");
+    }
+    int rc = install_schur(g, m, Rc);
+    cudaFree(Rc);
+    if (rc < 0) return rc;
+    if (eig_out)
+        for (int i = 0; i < 2 * m; ++i) eig_out[i] = g->lambda[i];
+    double rmax = 0.0;
+    for (int i = 0; i < m; ++i) rmax = std::max(rmax, right.resid[cand[i]]);
+    g->setup_resid = rmax;
+    g->setup_iters[0] = right.iters;
+    g->setup_iters[1] = 0;
+    g->setup_matvecs = right.matvecs;
+    if (!ok) {
+        char msg[200];
+        snprintf(msg, sizeof(msg),
+                 "deflate_setup_schur: pairs did not all reach tol (%s after %d iterations, worst residual %.2e); "
+                 "basis installed", right.converged ? "converged" : "not converged", right.iters, rmax);
+        return lib_fail(OVS_EEIG, msg);
+    }
+    return OVS_OK;
+}
+
 }  // namespace
 
-int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out) {
+int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
     Ctx c;
     c.g = g;
     c.st = 0;
@@ -465,9 +543,10 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out) {
 
     // right eigenvectors of H_w(mu)
     SideResult right, left;
-    const double side_s = g->setup_budget_s > 0.0 ? 0.5 * g->setup_budget_s : 0.0;
+    const double side_s = g->setup_budget_s > 0.0 ? (schur ? 1.0 : 0.5) * g->setup_budget_s : 0.0;
     int rc = run_side(c, m, tol, g->mu, 12345, side_s, right);
     if (rc) SETUP_FAIL(rc);
+    if (schur) return finish_schur(c, g, m, tol, right, eig_out);
     double2* Rblk = nullptr;
     if (cudaMalloc((void**)&Rblk, blk) != cudaSuccess) return lib_fail(OVS_ENOMEM, "deflate_setup: right block");
     cudaMemcpy(Rblk, c.Q, blk, cudaMemcpyDeviceToDevice);

@@ -41,8 +41,15 @@ struct KryWork {  // Krylov basis and small matrices
     void* coeff = nullptr;  // [nrhs][kmax] complex128
     void* newton = nullptr; // [nrhs][2 kmax^2] complex128
     void* cdef = nullptr;   // [nrhs][m] complex128 deflation coefficients
-    void* cdef2 = nullptr;  // [nrhs][m] complex128 sgn-scaled
+    void* cdef2 = nullptr;  // [nrhs][m] complex128 sgn-scaled (Schur: second-pass scratch)
+    int mdef = 0;           // m the deflation buffers below were sized for
+    void* X = nullptr;      // Schur: [nrhs][m x kmax] complex128, X = S^H H_w V_k (column-major)
+    void* sylv = nullptr;   // Schur: [nrhs][2 m 800] complex128 Sylvester scratch (C, Y)
+    void* cS = nullptr;     // Schur: [nrhs][m] complex128 coefficients of S in y
 };
+
+// deflation scheme installed on a handle
+enum { DEFL_NONE = 0, DEFL_LR = 1, DEFL_SCHUR = 2 };
 
 struct ovs_gauge_s {
     int dims[4];
@@ -54,8 +61,13 @@ struct ovs_gauge_s {
     double mu = 0.0, m_w = 0.0, kappa = 0.0;
     void* links64 = nullptr;  // [4][9][V] double2
     void* links32 = nullptr;  // [4][9][V] float2 (OVS_MIXED)
-    // deflation basis (internal layout)
+    // deflation basis (internal layout). LR: R (right eigenvectors) and L
+    // (left, biorthonormalised). Schur: R holds the Schur vectors S_m, L is
+    // absent, schurT / schurFT are T_m and sgn(T_m) (column-major m x m).
     int m = 0;
+    int scheme = DEFL_NONE;
+    void* schurT = nullptr;
+    void* schurFT = nullptr;
     void* R64 = nullptr;  // [m][N] double2 planes
     void* L64 = nullptr;  // biorthonormalised
     void* R32 = nullptr;  // [m][N/2] float4 planes
@@ -112,6 +124,11 @@ int lib_fail(int code, const char* msg);
 // Install R (right) and L (left) vectors given as device canonical
 // complex128 [m][N]; L is biorthonormalised against R.
 int install_deflation(ovs_gauge_s* g, int m, const void* Rc, const void* Lc, const double* lambda);
+// Install Schur deflation from m right vectors (device canonical complex128
+// [m][N]): S_m, T_m = S_m^H H_w S_m and sgn(T_m) (schur.cu).
+int install_schur(ovs_gauge_s* g, int m, const void* Rc);
+// Drop the deflation basis (and the recorded applications that used it).
+void free_deflation(ovs_gauge_s* g);
 // Stencil shape for (tp, nrhs) on this handle: the cached choice, else (not
 // capturing) the fastest candidate timed on st with in -> out as operands.
 StencilShape stencil_shape(ovs_gauge_s* g, int tp, int nrhs, const void* in, size_t in_stride, void* out,

@@ -45,6 +45,9 @@ cudaError_t launch_to_internal(int prec, const void* canon, size_t canon_stride_
                                int V, int nrhs, cudaStream_t st);
 cudaError_t launch_to_canonical(int prec, const void* in, size_t in_stride, void* canon, size_t canon_stride_cplx,
                                 int V, int nrhs, cudaStream_t st);
+// canon = x + gamma5 * in (in: internal complex128 planes): D_ov's last step
+cudaError_t launch_to_canonical_overlap(const void* in, size_t in_stride, const void* x, size_t x_stride_cplx,
+                                        void* canon, size_t canon_stride_cplx, int V, int nrhs, cudaStream_t st);
 cudaError_t launch_links_to_internal(const void* canon, void* u64, void* u32, int V, cudaStream_t st);
 cudaError_t launch_links_to_canonical(const void* u64, void* canon, int V, cudaStream_t st);
 
@@ -148,6 +151,37 @@ cudaError_t launch_sign_scale(const void* c, const double* sgn, int m, int nrhs,
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
                           int* status, cudaStream_t st, const int* active = nullptr, int n_fixed = 0);
+// harmonic variant: H_r[:, k-1] += |h_(k+1,k)|^2 H_k^-H e_k (k = k_used[r]);
+// work as for launch_newton (used as scratch before it)
+cudaError_t launch_harmonic(void* H, long long h_rhs_stride, int ldh, const int* k_used, void* work, int kmax,
+                            int nrhs, cudaStream_t st);
+// ---- Schur deflation (schur.cu)
+// X[:, j] = (X[:, j] - X[:, <j] s) / beta_j, s = red[r][0..j)
+cudaError_t launch_schur_xcol(void* X, long long x_rhs, int m, int j, const void* red, long long red_stride,
+                              const double* inv_beta, const int* active, int nrhs, cudaStream_t st);
+// cS_r = sgn(T) c_r + beta_r Y_r e_1, Y_r from T Y - Y H_k = sgn(T) X - X sgn(H_k)
+bool schur_coeff_fits(int kmax);
+long long schur_scratch_per_rhs(int m);
+cudaError_t launch_schur_coeff(const void* T, const void* fT, int m, const void* X, long long x_rhs, const void* H,
+                               long long h_rhs, int ldh, const void* fH, long long fh_rhs, const int* k_used,
+                               const int* status, const double* beta, const void* c, long long c_stride,
+                               void* scratch, void* cS, long long cs_stride, int nrhs, cudaStream_t st);
+// ---- outer GMRES of the overlap solve (solve.cu); canonical complex128
+int norm_blocks();  // partials per right-hand side of the norm kernels
+// norm[r] = ||v_r||, inv[r] = 1/norm[r] (inv may be nullptr); partial: nrhs x norm_blocks()
+cudaError_t launch_norms(const void* v, long long n, long long stride, int nrhs, double* partial, double* norm,
+                         double* inv, cudaStream_t st);
+cudaError_t launch_norm_partials(const void* v, long long n, long long stride, int nrhs, double* partial,
+                                 cudaStream_t st);
+cudaError_t launch_scale(const void* in, long long in_stride, void* out, long long out_stride, const double* s,
+                         long long n, int nrhs, cudaStream_t st);
+cudaError_t launch_sub(const void* a, const void* b, void* out, long long n, int nrhs, cudaStream_t st);
+cudaError_t launch_gmres_start(const double* beta, void* gv, int restart, int nrhs, cudaStream_t st);
+cudaError_t launch_gmres_col(const void* red1, const void* red2, long long red_stride, const double* npart, int j,
+                             int restart, void* R, void* rot, void* gv, double* est, double* inv_hn, int nrhs,
+                             cudaStream_t st);
+cudaError_t launch_gmres_backsub(const void* R, const void* gv, int jj, int restart, void* y, int nrhs,
+                                 cudaStream_t st);
 // est[r] = ||cnew_r - cold_r|| / ||cnew_r||; below tol: active[r] = 0, k_used[r] = n
 cudaError_t launch_conv_check(const void* cnew, const void* cold, long long stride, int n, double tol, int* active,
                               int* k_used, double* est, int nrhs, cudaStream_t st);

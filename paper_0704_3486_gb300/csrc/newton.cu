@@ -491,6 +491,93 @@ cudaError_t launch_conv_check(const void* cnew, const void* cold, long long stri
     return cudaGetLastError();
 }
 
+// Harmonic variant (the see-saw-free form cited in Sec. 4): H_k is replaced
+// by H^_k = H_k + |h_(k+1,k)|^2 f e_k^T with f = H_k^-H e_k, whose
+// eigenvalues are the harmonic Ritz values. One block per right-hand side.
+// f from a Givens QR of the Hessenberg H_k: rotations G_j (rows j, j+1)
+// with G_(k-2) ... G_0 H_k = R give H_k = Q R, Q = G_0^H ... G_(k-2)^H, and
+// H_k^H f = e_k is R^H (Q^H f) = e_k, so f = Q e_k / conj(R_kk). The copy of
+// H_k and the rotations live in `work` (2 kmax^2 complex128 per right-hand
+// side, the Newton work space, free before the Newton kernel runs).
+// Right-hand sides after a breakdown (h_(k+1,k) = 0) keep H_k.
+__global__ void __launch_bounds__(256) k_harmonic(double2* __restrict__ H, long long h_rhs_stride, int ldh,
+                                                  const int* __restrict__ k_used, double2* __restrict__ work,
+                                                  int kmax) {
+    __shared__ double2 s_rot[2];
+    const int r = blockIdx.x, tid = threadIdx.x;
+    const int n = k_used[r];
+    double2* Hr = H + r * h_rhs_stride;
+    if (n < 1) return;
+    const double2 sub = Hr[n + (long long)(n - 1) * ldh];
+    const double h2 = sub.x * sub.x + sub.y * sub.y;
+    if (!(h2 > 0.0)) return;
+    cd* W = reinterpret_cast<cd*>(work) + (size_t)r * 2 * kmax * kmax;  // row-major n x n
+    cd* rot = W + (size_t)kmax * kmax;                                // (a/rho, b/rho) per step
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx - i * n;
+        const double2 h = (i <= j + 1) ? Hr[i + (long long)j * ldh] : make_double2(0.0, 0.0);
+        W[idx] = {h.x, h.y};
+    }
+    __syncthreads();
+    for (int j = 0; j + 1 < n; ++j) {
+        if (tid == 0) {
+            const cd a = W[(size_t)j * n + j], b = W[(size_t)(j + 1) * n + j];
+            const double rho = sqrt(a.re * a.re + a.im * a.im + b.re * b.re + b.im * b.im);
+            if (rho > 0.0 && isfinite(rho)) {
+                s_rot[0] = make_double2(a.re / rho, a.im / rho);
+                s_rot[1] = make_double2(b.re / rho, b.im / rho);
+            } else {
+                s_rot[0] = make_double2(1.0, 0.0);
+                s_rot[1] = make_double2(0.0, 0.0);
+            }
+            rot[2 * j] = {s_rot[0].x, s_rot[0].y};
+            rot[2 * j + 1] = {s_rot[1].x, s_rot[1].y};
+        }
+        __syncthreads();
+        // G = [[conj(a), conj(b)], [-b, a]] / rho on rows j, j+1
+        const cd ca = {s_rot[0].x, s_rot[0].y}, cb = {s_rot[1].x, s_rot[1].y};
+        for (int l = j + tid; l < n; l += blockDim.x) {
+            const cd w1 = W[(size_t)j * n + l], w2 = W[(size_t)(j + 1) * n + l];
+            W[(size_t)j * n + l] = cmulc(ca, w1) + cmulc(cb, w2);
+            W[(size_t)(j + 1) * n + l] = cmul(ca, w2) - cmul(cb, w1);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        // v = Q e_n = G_0^H ... G_(n-2)^H e_n; G^H = [[a, -conj(b)], [b, conj(a)]] / rho
+        cd* v = W;  // row 0 of W is no longer needed: reuse it for v
+        const cd rnn = W[(size_t)(n - 1) * n + (n - 1)];
+        for (int i = 0; i < n; ++i) v[i] = {0.0, 0.0};
+        v[n - 1] = {1.0, 0.0};
+        for (int j = n - 2; j >= 0; --j) {
+            const cd a = rot[2 * j], b = rot[2 * j + 1];
+            const cd v1 = v[j], v2 = v[j + 1];
+            v[j] = cmul(a, v1) - cmulc(b, v2);
+            v[j + 1] = cmul(b, v1) + cmulc(a, v2);
+        }
+        // f = v / conj(rnn); H[:, n-1] += |h|^2 f
+        const double den = rnn.re * rnn.re + rnn.im * rnn.im;
+        if (den > 0.0 && isfinite(den)) {
+            const cd inv_conj = {rnn.re / den, rnn.im / den};  // 1 / conj(rnn) = rnn / |rnn|^2
+            for (int i = 0; i < n; ++i) {
+                const cd f = cmul(v[i], inv_conj);
+                double2 h = Hr[i + (long long)(n - 1) * ldh];
+                h.x += h2 * f.re;
+                h.y += h2 * f.im;
+                Hr[i + (long long)(n - 1) * ldh] = h;
+            }
+        }
+    }
+    // a singular H_k (R_kk = 0) is left unmodified: the Newton iteration on
+    // it then reports OVS_ESIGN
+}
+
+cudaError_t launch_harmonic(void* H, long long h_rhs_stride, int ldh, const int* k_used, void* work, int kmax,
+                            int nrhs, cudaStream_t st) {
+    k_harmonic<<<nrhs, 256, 0, st>>>((double2*)H, h_rhs_stride, ldh, k_used, (double2*)work, kmax);
+    return cudaGetLastError();
+}
+
 static size_t cluster_smem(int kmax, int ncl) {
     const int Wmax = (kmax + ncl - 1) / ncl;
     return ((size_t)kmax * Wmax + 3 * (size_t)kmax + Wmax) * sizeof(cd) + 2 * (size_t)kmax * sizeof(int);

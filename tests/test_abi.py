@@ -97,3 +97,15 @@ def test_stencil_shapes_and_trace_classes_match_header():
     classes = re.findall(r"OVS_PROF_([A-Z]+)\s*=\s*(\d+)", text)
     named = {int(v): n.lower() for n, v in classes if n != "NCLASS"}
     assert [named[i] for i in range(len(named))] == ovs.PROF_CLASSES
+
+
+def test_solve_struct_layouts_and_flags():
+    import ctypes
+    import re
+
+    import paper_0704_3486_gb300 as ovs
+    assert ctypes.sizeof(ovs.SolveOpts) == 16
+    assert ctypes.sizeof(ovs.SolveInfo) == 24
+    text = open(os.path.join(ROOT, "include", "ovsign.h")).read()
+    m = re.search(r"#define\s+OVS_APPLY_HARMONIC\s+(\d+)", text)
+    assert m and int(m.group(1)) == ovs.APPLY_HARMONIC

@@ -9,11 +9,13 @@ The lattices 8^4 (N = 49,152), 12^4 (N = 248,832) and 16^3 x 32
   per-site sum of Eq. Dw, links from the seeded generator on both sides;
   relative 2-norm over the sampled entries 1e-13 (FP64) and 2e-6 (mixed);
 * free field at 16^3 x 32: every entry against the FFT closed form;
-* LR-deflated sign application at 8^4 (m = 30, k = 200, FP64): against the
-  oracle's CGS2 Arnoldi at equal (m, k), 1e-12; the mixed form 1e-6. The
+* LR-deflated sign application at 8^4 (m = 30, k = 200, 4 RHS) and 12^4
+  (m = 50, k = 250, 16 RHS; four of them checked): against the oracle's
+  CGS2 Arnoldi at equal (m, k), 1e-12 (FP64) and 1e-6 (mixed). The
   deflation vectors are seeded synthetic inputs, not eigenvectors: the
   formula of Sec. 5.3 is defined for any biorthonormalisable pair (R, L),
   and both sides receive the same arrays;
+* the plain method at 4^4, k = 300: against the oracle and the dense sign;
 * 12^4 (m = 50) and 16^3 x 32 (m = 100, the timed workload): the mixed
   16-RHS application against the FP64 single-RHS application at equal
   (m, k), with the deflation basis of the device set-up, 1e-6.
@@ -121,15 +123,111 @@ def test_deflated_sign_8to4_matches_oracle(gpu):
     R, L, lam = synthetic_deflation(n, m, 301)
     gpu.deflate_load(g, R.T.copy(), L.T.copy(), lam)
     x = synth.gaussian_vectors(n, nrhs, 303)
-    ref, _ = deflation.lr_sign_apply(lambda q: h @ q, x[0], R, L, lam, k)
+    refs = [deflation.lr_sign_apply(lambda q: h @ q, x[r], R, L, lam, k)[0] for r in range(nrhs)]
     xd = torch.from_numpy(x).to(DEV)
     yd = torch.empty_like(xd)
     st, info = gpu.sign_apply(g, xd, yd, k, prec=gpu.F64)
-    assert st == 0 and info[0]["k_used"] == k
-    assert rel(yd.cpu().numpy()[0], ref) < 1e-12
+    assert st == 0 and all(i["k_used"] == k for i in info)
+    y = yd.cpu().numpy()
+    for r in range(nrhs):
+        assert rel(y[r], refs[r]) < 1e-12, r
     st, info = gpu.sign_apply(g, xd, yd, k, prec=gpu.MIXED)
     assert st == 0
-    assert rel(yd.cpu().numpy()[0], ref) < 1e-6
+    y = yd.cpu().numpy()
+    for r in range(nrhs):
+        assert rel(y[r], refs[r]) < 1e-6, r
+    g.destroy()
+
+
+def _oracle_12to4(r):
+    """Oracle result for right-hand side r of the 12^4 parity case (run in a
+    spawned worker: it rebuilds every input from its seed)."""
+    import numpy as np_
+
+    import synth as synth_
+    from oracle import deflation as deflation_, lattice as lattice_
+    dims, seed, eps, mu = (12, 12, 12, 12), 4, 0.7, 0.2
+    n = 12 * 12 ** 4
+    links = synth_.gauge_links(dims, seed, eps)
+    h = lattice_.hw_operator(links, dims, mu, MW)
+    R, L, lam = synthetic_deflation(n, 50, 401)
+    x = synth_.gaussian_vectors(n, 16, 403)[r]
+    y, _ = deflation_.lr_sign_apply(lambda q: h @ q, x, R, L, lam, 250)
+    return np_.asarray(y)
+
+
+def test_deflated_sign_12to4_sixteen_rhs_matches_oracle(gpu):
+    """12^4 (N = 248,832), m = 50 loaded vectors, k = 250, 16 right-hand
+    sides in one call (the timed workload's launch configuration: the
+    16-RHS Newton cluster size, the chunked inner-product sweep over 16 RHS,
+    the TMA recombination): right-hand sides 0, 5, 10 and 15 against the
+    oracle at equal (m, k), FP64 1e-12 and mixed 1e-6; the oracle runs in
+    four spawned processes."""
+    import multiprocessing as mp
+    dims, seed, eps, mu = CONFIGS["12^4"]
+    n, m, k, nrhs = 12 * 12 ** 4, 50, 250, 16
+    import os
+    check = (0, 5, 10, 15)
+    ctx = mp.get_context("spawn")
+    # the workers' BLAS threads share the host cores (inherited at spawn)
+    saved = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = str(max(1, (os.cpu_count() or 4) // len(check)))
+    try:
+        pool = ctx.Pool(len(check))
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    with pool:
+        pending = pool.map_async(_oracle_12to4, check)
+        g = gpu.create_gauge(dims, seed, eps, gpu.MIXED)
+        gpu.set_mu(g, mu, MW)
+        R, L, lam = synthetic_deflation(n, m, 401)
+        gpu.deflate_load(g, R.T.copy(), L.T.copy(), lam)
+        x = synth.gaussian_vectors(n, nrhs, 403)
+        xd = torch.from_numpy(x).to(DEV)
+        yd = torch.empty_like(xd)
+        st, info = gpu.sign_apply(g, xd, yd, k, prec=gpu.F64)
+        assert st == 0 and all(i["k_used"] == k for i in info)
+        y64 = yd.cpu().numpy()
+        st, info = gpu.sign_apply(g, xd, yd, k, prec=gpu.MIXED)
+        assert st == 0 and all(i["k_used"] == k for i in info)
+        y32 = yd.cpu().numpy()
+        g.destroy()
+        refs = pending.get(timeout=1800)
+    for r, ref in zip(check, refs):
+        assert rel(y64[r], ref) < 1e-12, r
+        assert rel(y32[r], ref) < 1e-6, r
+
+
+def test_undeflated_4to4_k300_against_dense_sign(gpu):
+    """The plain method on the tiny configuration (4^4, eps 0.5, seed 1,
+    mu 0.3, m = 0), FP64, k = 300: against the oracle's CGS2 Arnoldi at
+    equal k (1e-12), and its error against the dense spectral sign equals
+    the oracle's (the truncation of the method at this k, about 3e-6)."""
+    from oracle import arnoldi, signfun
+    dims, mu = (4, 4, 4, 4), 0.3
+    links = synth.gauge_links(dims, 1, 0.5)
+    h = lattice.hw_operator(links, dims, mu, MW)
+    g = gpu.create_gauge_from_links(dims, links, gpu.F64)
+    gpu.set_mu(g, mu, MW)
+    x = np.concatenate([synth.gaussian_vectors(3072, 1, 2), synth.ones_vector(3072) / np.sqrt(3072)])
+    xd = torch.from_numpy(x).to(DEV)
+    yd = torch.empty_like(xd)
+    st, info = gpu.sign_apply(g, xd, yd, 300, prec=gpu.F64)
+    assert st == 0
+    y = yd.cpu().numpy()
+    hd = h.toarray()
+    dec = signfun.eig_decomposition(hd)
+    for r in range(2):
+        ref, _ = arnoldi.arnoldi_sign(lambda q: h @ q, x[r], 300)
+        assert rel(y[r], ref) < 1e-12, r
+        exact = signfun.sgn_apply_dense(hd, x[r], dec)
+        e_gpu, e_cpu = rel(y[r], exact), rel(ref, exact)
+        assert abs(e_gpu - e_cpu) <= 1e-3 * e_cpu + 1e-12 and e_gpu < 1e-4, (r, e_gpu, e_cpu)
     g.destroy()
 
 
