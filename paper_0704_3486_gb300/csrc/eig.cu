@@ -67,6 +67,31 @@ __global__ void k_ritz_resid(const double2* __restrict__ Z, const double2* __res
     }
 }
 
+// the same for complex64 blocks, accumulated in FP64
+__global__ void k_ritz_resid32(const float2* __restrict__ Z, const float2* __restrict__ X,
+                               const double2* __restrict__ theta, long long N, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x;
+    const double2 t = theta[i];
+    const float2* z = Z + (size_t)i * N;
+    const float2* x = X + (size_t)i * N;
+    double s = 0.0;
+    for (long long n = threadIdx.x; n < N; n += blockDim.x) {
+        const float2 a = z[n], b = x[n];
+        const double rx = (double)a.x - (t.x * b.x - t.y * b.y);
+        const double ry = (double)a.y - (t.x * b.y + t.y * b.x);
+        s += rx * rx + ry * ry;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+        out[i] = sqrt(tot);
+    }
+}
+
 // U[:, j] *= 1/sqrt(max(lam_j, floor)) (column-major p x p)
 __global__ void k_scale_cols(double2* __restrict__ U, const double* __restrict__ lam, int p, double floor_) {
     const int j = blockIdx.x;
@@ -91,6 +116,7 @@ struct Ctx {
     double2 *Q = nullptr, *W = nullptr, *A1 = nullptr, *A2 = nullptr;  // [p][N] complex128
     void* F[3] = {nullptr, nullptr, nullptr};                            // [p][N] complex64 filter buffers
     double2 *G = nullptr, *G2 = nullptr, *Y = nullptr, *theta = nullptr;
+    float2 *G32 = nullptr, *Y32 = nullptr;  // p x p complex64 copies for the complex64 block algebra
     double* lam = nullptr;
     double* resid = nullptr;
     int* info = nullptr;
@@ -100,7 +126,7 @@ struct Ctx {
     char err[256] = {0};
     ~Ctx() {
         for (void* q : {(void*)Q, (void*)W, (void*)A1, (void*)A2, F[0], F[1], F[2], (void*)G, (void*)G2, (void*)Y,
-                        (void*)theta, (void*)lam, (void*)resid, (void*)info, dwork})
+                        (void*)theta, (void*)lam, (void*)resid, (void*)info, dwork, (void*)G32, (void*)Y32})
             if (q) cudaFree(q);
         if (params) cusolverDnDestroyParams(params);
         if (cs) cusolverDnDestroy(cs);
@@ -246,6 +272,89 @@ int rayleigh_ritz(Ctx& c, double mu, std::vector<std::complex<double>>& theta, s
     return OVS_OK;
 }
 
+const cuComplex kOneF = {1.0f, 0.0f}, kZeroF = {0.0f, 0.0f};
+
+// SVQB of a complex64 block, twice: G = Q^H Q by CGEMM, its eigen-
+// decomposition in complex128, Q <- Q U diag(lam)^-1/2 by CGEMM. Q and tmp
+// are swapped as needed; on return Q points at the orthonormal block.
+int svqb32(Ctx& c, void*& Q, void*& tmp) {
+    const int p = c.p;
+    const long long N = c.N;
+    for (int pass = 0; pass < 2; ++pass) {
+        BCK(cublasCgemm(c.cb, CUBLAS_OP_C, CUBLAS_OP_N, p, p, (int)N, &kOneF, (const cuComplex*)Q, (int)N,
+                        (const cuComplex*)Q, (int)N, &kZeroF, (cuComplex*)c.G32, p));
+        ECK(launch_convert(PREC_F64, c.G32, c.G, (long long)p * p, c.st));
+        int lwork = 0;
+        BCK(cusolverDnZheevd_bufferSize(c.cs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p,
+                                        (cuDoubleComplex*)c.G, p, c.lam, &lwork));
+        if ((size_t)lwork * 16 > c.dwork_bytes) {
+            if (c.dwork) cudaFree(c.dwork);
+            c.dwork_bytes = (size_t)lwork * 16;
+            ECK(cudaMalloc(&c.dwork, c.dwork_bytes));
+        }
+        BCK(cusolverDnZheevd(c.cs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, p, (cuDoubleComplex*)c.G, p,
+                             c.lam, (cuDoubleComplex*)c.dwork, lwork, c.info));
+        std::vector<double> lam(p);
+        ECK(cudaMemcpyAsync(lam.data(), c.lam, sizeof(double) * p, cudaMemcpyDeviceToHost, c.st));
+        ECK(cudaStreamSynchronize(c.st));
+        const double floor_ = std::max(lam[p - 1], 1e-300) * 1e-12;
+        k_scale_cols<<<p, 128, 0, c.st>>>(c.G, c.lam, p, floor_);
+        ECK(cudaGetLastError());
+        ECK(launch_convert(PREC_F32, c.G, c.G32, (long long)p * p, c.st));
+        BCK(cublasCgemm(c.cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, p, p, &kOneF, (const cuComplex*)Q, (int)N,
+                        (const cuComplex*)c.G32, p, &kZeroF, (cuComplex*)tmp, (int)N));
+        std::swap(Q, tmp);
+    }
+    return OVS_OK;
+}
+
+// Rayleigh-Ritz of H_w(mu) on the complex64 orthonormal block Q: Z = H Q
+// (complex64 stencil), G = Q^H Z (CGEMM), the p x p eigenproblem in
+// complex128, Ritz vectors X = Q Y and Z Y (CGEMM), residual norms
+// ||Z y - theta Q y|| summed in FP64. Buffers Z, X, ZX: p x N complex64.
+int rayleigh_ritz32(Ctx& c, double mu, void* Q, void* Z, void* X, void* ZX,
+                    std::vector<std::complex<double>>& theta, std::vector<double>& resid) {
+    const int p = c.p;
+    const long long N = c.N;
+    int rc = apply_h(c, PREC_F32, Q, Z, mu);
+    if (rc) return rc;
+    BCK(cublasCgemm(c.cb, CUBLAS_OP_C, CUBLAS_OP_N, p, p, (int)N, &kOneF, (const cuComplex*)Q, (int)N,
+                    (const cuComplex*)Z, (int)N, &kZeroF, (cuComplex*)c.G32, p));
+    ECK(launch_convert(PREC_F64, c.G32, c.G, (long long)p * p, c.st));
+    size_t dbytes = 0, hbytes = 0;
+    BCK(cusolverDnXgeev_bufferSize(c.cs, c.params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, p,
+                                   CUDA_C_64F, c.G, p, CUDA_C_64F, c.theta, CUDA_C_64F, nullptr, p, CUDA_C_64F, c.Y,
+                                   p, CUDA_C_64F, &dbytes, &hbytes));
+    if (dbytes > c.dwork_bytes) {
+        if (c.dwork) cudaFree(c.dwork);
+        c.dwork_bytes = dbytes;
+        ECK(cudaMalloc(&c.dwork, c.dwork_bytes));
+    }
+    if (hbytes > c.hwork.size()) c.hwork.resize(hbytes);
+    BCK(cusolverDnXgeev(c.cs, c.params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, p, CUDA_C_64F, c.G, p,
+                        CUDA_C_64F, c.theta, CUDA_C_64F, nullptr, p, CUDA_C_64F, c.Y, p, CUDA_C_64F, c.dwork,
+                        c.dwork_bytes, c.hwork.empty() ? nullptr : c.hwork.data(), c.hwork.size(), c.info));
+    int info = 0;
+    ECK(cudaMemcpyAsync(&info, c.info, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    ECK(launch_convert(PREC_F32, c.Y, c.Y32, (long long)p * p, c.st));
+    BCK(cublasCgemm(c.cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, p, p, &kOneF, (const cuComplex*)Q, (int)N,
+                    (const cuComplex*)c.Y32, p, &kZeroF, (cuComplex*)X, (int)N));
+    BCK(cublasCgemm(c.cb, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, p, p, &kOneF, (const cuComplex*)Z, (int)N,
+                    (const cuComplex*)c.Y32, p, &kZeroF, (cuComplex*)ZX, (int)N));
+    k_ritz_resid32<<<p, 256, 0, c.st>>>((const float2*)ZX, (const float2*)X, c.theta, N, c.resid);
+    ECK(cudaGetLastError());
+    theta.resize(p);
+    resid.resize(p);
+    ECK(cudaMemcpyAsync(theta.data(), c.theta, sizeof(double2) * p, cudaMemcpyDeviceToHost, c.st));
+    ECK(cudaMemcpyAsync(resid.data(), c.resid, sizeof(double) * p, cudaMemcpyDeviceToHost, c.st));
+    ECK(cudaStreamSynchronize(c.st));
+    if (info != 0) {
+        snprintf(c.err, sizeof(c.err), "geev info = %d", info);
+        return OVS_EEIG;
+    }
+    return OVS_OK;
+}
+
 struct SideResult {
     std::vector<std::complex<double>> theta;
     std::vector<double> resid;
@@ -298,7 +407,13 @@ struct FilterPlan {
     int deg;
 };
 
-FilterPlan plan_filter(double b, double lm, double a, double kappa, double mu, double eta_near) {
+// lmin: the smallest |theta|^2 of the block; range: the largest ratio of
+// the filter's gains at lmin and at lm that the working precision keeps
+// (the filter damps a wanted vector relative to the smallest one by that
+// ratio; beyond the precision's range the wanted vector is lost to
+// rounding); dmax: a cap on the degree.
+FilterPlan plan_filter(double b, double lm, double a, double kappa, double mu, double eta_near, double lmin,
+                       double range, int dmax) {
     const double eta_glob = 4.0 * kappa * std::sinh(std::fabs(mu));
     eta_near = std::min(eta_near, eta_glob);
     const double aE = 0.5 * (lm + a);
@@ -325,8 +440,11 @@ FilterPlan plan_filter(double b, double lm, double a, double kappa, double mu, d
     const double w = (cc - lm) / fp.e;
     const double rho_w = w > 1.0 ? w + std::sqrt(w * w - 1.0) : 1.0;
     const double gain = rho_w / rho_ell;
-    const double d = gain > 1.0 + 1e-9 ? std::log(1e3) / std::log(gain) : 3000.0;
-    fp.deg = (int)std::min(std::max(d, 16.0), 3000.0);
+    double d = gain > 1.0 + 1e-9 ? std::log(1e3) / std::log(gain) : (double)dmax;
+    const double w0 = (cc - lmin) / fp.e;
+    const double rho_0 = w0 > 1.0 ? w0 + std::sqrt(w0 * w0 - 1.0) : 1.0;
+    if (rho_0 > rho_w * (1.0 + 1e-12)) d = std::min(d, std::log(range) / std::log(rho_0 / rho_w));
+    fp.deg = (int)std::min(std::max(d, 16.0), (double)dmax);
     return fp;
 }
 
@@ -350,14 +468,71 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
     ECK(launch_random_fill(c.Q, (long long)p * N, seed, c.st));
     rc = svqb(c);
     if (rc) return rc;
-    int fprec = (g->prec == OVS_MIXED && g->links32 != nullptr) ? PREC_F32 : PREC_F64;
-    FilterPlan fp = plan_filter(b, 0.01 * b, 0.02 * b, g->kappa, mu, 1e300);
+    // complex64 phase: filter, orthonormalisation and Rayleigh-Ritz all in
+    // complex64 (CGEMM on the CUDA cores; GB300's FP64 rate is 1/58 of its
+    // FP32 rate), with a complex128 Rayleigh-Ritz to certify the pairs;
+    // complex128 filtering only if complex64 stops making progress
+    bool c64 = (g->prec == OVS_MIXED && g->links32 != nullptr);
+    const double kRange32 = 1e4, kRange64 = 1e9;
+    const int kDmax32 = 800, kDmax64 = 3000;
+    FilterPlan fp = plan_filter(b, 0.01 * b, 0.02 * b, g->kappa, mu, 1e300, 0.0, c64 ? kRange32 : kRange64,
+                                c64 ? kDmax32 : kDmax64);
     const long long budget = 400000LL * std::max(1, (int)std::ceil(8.0e6 / (double)N)) + 200LL * p * 3000;
-    double last_rmax = 1e300;
+    double last_rmax = 1e300, last_rmax32 = 1e300;
     int last_deg = fp.deg;
-    const int max_iter = 40;
+    const int max_iter = 60;
     std::vector<int> order(p);
     double last_iter_s = 0.0;
+    bool have64 = false;  // the last pairs come from a complex128 Rayleigh-Ritz (Q holds them)
+    bool switched = false;  // this iteration left complex64
+    if (c64) ECK(launch_convert(PREC_F32, c.Q, c.F[0], (long long)p * N, c.st));
+    auto sort_order = [&]() {
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(),
+                  [&](int x, int y) { return std::abs(res.theta[x]) < std::abs(res.theta[y]); });
+    };
+    auto max_resid = [&]() {
+        double r = 0.0;
+        for (int i = 0; i < m; ++i) r = std::max(r, res.resid[order[i]] / hnorm);
+        return r;
+    };
+    // progress measure: the median residual of the m wanted pairs (the
+    // largest one, at the edge of the wanted set, converges slowest)
+    auto median_resid = [&]() {
+        std::vector<double> rr(m);
+        for (int i = 0; i < m; ++i) rr[i] = res.resid[order[i]] / hnorm;
+        std::nth_element(rr.begin(), rr.begin() + m / 2, rr.end());
+        return rr[m / 2];
+    };
+    auto report = [&](int it, const char* what, double rmax) {
+        if (!log) return;
+        std::vector<double> rr(m);
+        for (int i = 0; i < m; ++i) rr[i] = res.resid[order[i]] / hnorm;
+        std::sort(rr.begin(), rr.end());
+        int nconv = 0;
+        for (int i = 0; i < m; ++i) nconv += rr[i] <= tol;
+        std::fprintf(stderr,
+                     "[setup] mu=%+.3f it=%d deg=%d %s |theta| min=%.4e m-th=%.4e p-th=%.4e resid max=%.3e "
+                     "median=%.3e converged=%d/%d elapsed=%.2fs\n",
+                     mu, it + 1, fp.deg, what, std::abs(res.theta[order[0]]), std::abs(res.theta[order[m - 1]]),
+                     std::abs(res.theta[order[p - 1]]), rmax, rr[m / 2], nconv, m,
+                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+    };
+    // complex128 Rayleigh-Ritz of the block in Q (orthonormalised first);
+    // Q then holds the Ritz vectors
+    auto certify = [&](int it) -> int {
+        int r2 = svqb(c);
+        if (r2) return r2;
+        r2 = rayleigh_ritz(c, mu, res.theta, res.resid);
+        if (r2) return r2;
+        res.matvecs += p;
+        std::swap(c.Q, c.A1);
+        sort_order();
+        have64 = true;
+        const double rmax = max_resid();
+        report(it, "c128 Rayleigh-Ritz", rmax);
+        return OVS_OK;
+    };
     for (int it = 0; it < max_iter; ++it) {
         const auto t_iter = std::chrono::steady_clock::now();
         // stop before an iteration that would overrun the deadline (the
@@ -366,73 +541,82 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
             const double el = std::chrono::duration<double>(t_iter - t_start).count();
             if (el + last_iter_s > deadline_s) break;
         }
-        // 1. filter
-        int idx = 0;
-        if (fprec == PREC_F32) {
-            ECK(launch_convert(PREC_F32, c.Q, c.F[0], (long long)p * N, c.st));
+        double rmax = 0.0;
+        if (c64) {
+            // 1. filter (complex64), F[0] -> F[idx]
             void* bufs[3] = {c.F[0], c.F[1], c.F[2]};
+            int idx = 0;
             rc = cheb_filter(c, PREC_F32, bufs, fp.deg, fp.c, fp.e, mu, &idx);
             if (rc) return rc;
-            ECK(launch_convert(PREC_F64, bufs[idx], c.Q, (long long)p * N, c.st));
+            res.matvecs += 2LL * fp.deg * p;
+            // 2. orthonormalise, 3. Rayleigh-Ritz, all complex64
+            void* q = bufs[idx];
+            void* tmp = bufs[(idx + 1) % 3];
+            rc = svqb32(c, q, tmp);
+            if (rc) return rc;
+            rc = rayleigh_ritz32(c, mu, q, c.W, c.A1, c.A2, res.theta, res.resid);
+            if (rc) return rc;
+            res.matvecs += p;
+            ECK(cudaMemcpyAsync(c.F[0], c.A1, sizeof(float2) * p * N, cudaMemcpyDeviceToDevice, c.st));
+            have64 = false;
+            sort_order();
+            const double r32 = max_resid();
+            report(it, "c64", r32);
+            const double med = median_resid();
+            const bool stalled = it > 0 && med > 0.7 * last_rmax32;
+            last_rmax32 = med;
+            rmax = r32;
+            if (r32 <= tol || stalled) {
+                // certify in complex128
+                ECK(launch_convert(PREC_F64, c.F[0], c.Q, (long long)p * N, c.st));
+                rc = certify(it);
+                if (rc) return rc;
+                rmax = max_resid();
+                if (rmax > tol && stalled) {
+                    c64 = false;  // complex64 has reached its limit: complex128 filtering from here,
+                    switched = true;  // whose stencil is FP64-ALU bound and ~20x slower per degree
+                } else if (rmax > tol) {
+                    ECK(launch_convert(PREC_F32, c.Q, c.F[0], (long long)p * N, c.st));
+                }
+            }
         } else {
             void* bufs[3] = {c.Q, c.A1, c.A2};
+            int idx = 0;
             rc = cheb_filter(c, PREC_F64, bufs, fp.deg, fp.c, fp.e, mu, &idx);
             if (rc) return rc;
             if (idx != 0) ECK(cudaMemcpyAsync(c.Q, bufs[idx], sizeof(double2) * p * N, cudaMemcpyDeviceToDevice, c.st));
+            res.matvecs += 2LL * fp.deg * p;
+            rc = certify(it);
+            if (rc) return rc;
+            rmax = max_resid();
         }
-        res.matvecs += 2LL * fp.deg * p;
-        // 2. orthonormalise, 3. Rayleigh-Ritz
-        rc = svqb(c);
-        if (rc) return rc;
-        rc = rayleigh_ritz(c, mu, res.theta, res.resid);
-        if (rc) return rc;
-        res.matvecs += p;
-        std::swap(c.Q, c.A1);  // Ritz vectors become the block
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(),
-                  [&](int x, int y) { return std::abs(res.theta[x]) < std::abs(res.theta[y]); });
-        double rmax = 0.0;
-        for (int i = 0; i < m; ++i) rmax = std::max(rmax, res.resid[order[i]] / hnorm);
         res.iters = it + 1;
-        if (log) {
-            double rmed = 0.0;
-            std::vector<double> rr(m);
-            for (int i = 0; i < m; ++i) rr[i] = res.resid[order[i]] / hnorm;
-            std::sort(rr.begin(), rr.end());
-            rmed = rr[m / 2];
-            int nconv = 0;
-            for (int i = 0; i < m; ++i) nconv += rr[i] <= tol;
-            std::fprintf(stderr,
-                         "[setup] mu=%+.3f it=%d deg=%d prec=%s |theta| m-th=%.4e p-th=%.4e resid max=%.3e "
-                         "median=%.3e converged=%d/%d elapsed=%.2fs\n",
-                         mu, it + 1, fp.deg, fprec == PREC_F32 ? "c64" : "c128", std::abs(res.theta[order[m - 1]]),
-                         std::abs(res.theta[order[p - 1]]), rmax, rmed, nconv, m,
-                         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
-        }
-        if (rmax <= tol) {
+        if (rmax <= tol && have64) {
             res.converged = true;
             break;
         }
         // 4. next filter: cut between the m-th and the last Ritz value of H^2
         const double lm2 = std::abs(res.theta[order[m - 1]] * res.theta[order[m - 1]]);
         const double ap2 = std::abs(res.theta[order[p - 1]] * res.theta[order[p - 1]]);
+        const double l02 = std::abs(res.theta[order[0]] * res.theta[order[0]]);
         double eta_near = 0.0;
         for (int i = 0; i < p; ++i) eta_near = std::max(eta_near, std::fabs(res.theta[i].imag()));
-        fp = plan_filter(b, lm2, std::max(ap2, 1.2 * lm2), g->kappa, mu, 1.5 * eta_near + 1e-12);
+        fp = plan_filter(b, lm2, std::max(ap2, 1.2 * lm2), g->kappa, mu, 1.5 * eta_near + 1e-12, l02,
+                         c64 ? kRange32 : kRange64, c64 ? kDmax32 : kDmax64);
         if (res.matvecs + 2LL * fp.deg * p > budget) break;
         // cost of the next iteration, scaled by its degree
         last_iter_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_iter).count() *
                       std::max(1.0, (double)fp.deg / std::max(1, last_deg));
+        if (switched) last_iter_s *= 20.0;
+        switched = false;
         last_deg = fp.deg;
-        // precision: complex64 until its rounding limits progress
-        // complex64 filtering until it stops making progress (FP32 rounding,
-        // or noise amplified by the filter): then complex128, whose stencil
-        // is FP64-ALU bound and costs ~20x more per degree
-        if (fprec == PREC_F32 && (rmax < 3e-6 || rmax > 0.5 * last_rmax)) {
-            fprec = PREC_F64;
-            last_iter_s *= 20.0;
-        }
         last_rmax = rmax;
+    }
+    if (!have64) {  // the last pairs are complex64 ones: certify them
+        ECK(launch_convert(PREC_F64, c.F[0], c.Q, (long long)p * N, c.st));
+        rc = certify(res.iters);
+        if (rc) return rc;
+        res.converged = max_resid() <= tol;
     }
     // hand the Ritz vectors (now in Q) to the caller, sorted by |theta|
     std::vector<std::complex<double>> th(p);
@@ -535,6 +719,8 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&c.G, sizeof(double2) * p * p);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c.G2, sizeof(double2) * p * p);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c.Y, sizeof(double2) * p * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.G32, sizeof(float2) * p * p);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.Y32, sizeof(float2) * p * p);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c.theta, sizeof(double2) * p);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c.lam, sizeof(double) * p);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c.resid, sizeof(double) * p);
