@@ -122,9 +122,14 @@ int ovs_matvec(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, 
  * (complex128, canonical layout, [nrhs][N]); host pointers fail with
  * OVS_EINVAL. The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. All calls share the array: calls that
- * overlap on the GPU race on it and must be serialised by the caller.
- * Same results as ovs_matvec; errors as ovs_matvec plus the size limit. */
+ * call before any stream capture. The address is kept for the life of the
+ * process: after a cudaDeviceReset of that device this entry point must not
+ * be called again. All calls share the array: calls that overlap on the GPU
+ * race on it and must be serialised by the caller. The current device must
+ * be the handle's, and x and y on it (else OVS_EINVAL). The stencil uses the
+ * launch shape the handle has chosen for (prec, nrhs), if any, without
+ * tuning. Same results as ovs_matvec; errors as ovs_matvec plus the size
+ * limit. */
 int ovs_matvec_noalloc(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_t nrhs, int32_t prec,
                        void* stream);
 
@@ -303,15 +308,17 @@ int ovs_get_krylov(ovs_gauge_t g, int32_t rhs, int32_t* k_out, double* V, double
 /* Batched form: n instances, each a handle with its own gauge field, mu and
  * deflation basis, and nrhs[i] right-hand sides x[i] -> y[i] (layout and
  * host/device rules of ovs_sign_apply; the n handles must be distinct).
- * The instances run concurrently: each on its handle's private stream,
- * forked from `stream` and joined back into it. Each instance's whole
- * application (A1-A7 of ovs_sign_apply, from an internal copy of x to an
- * internal y) is recorded once as a CUDA graph per (nrhs, opts) and
- * replayed; set_mu, deflation changes and buffer growth drop the recorded
- * graphs. With opts->check_every > 0 every right-hand side stops at its own
- * Krylov dimension (uneven depths). info, if not NULL, receives
- * sum(nrhs) reports in instance order; the call then waits for `stream`.
- * Returns the worst status as ovs_sign_apply. */
+ * Each instance's whole application (A1-A7 of ovs_sign_apply, from an
+ * internal copy of x to an internal y) is recorded once per (nrhs, opts) as
+ * a CUDA graph; the recorded applications of the n instances are the child
+ * graphs of one combined graph, built once per set of instances, nrhs and
+ * opts, so one graph launch on `stream` runs all instances concurrently
+ * (lattices of different sizes, uneven Krylov depths). set_mu, deflation
+ * changes and buffer growth drop the recorded graphs, ovs_destroy the
+ * combined ones that contain the handle. With opts->check_every > 0 every
+ * right-hand side stops at its own Krylov dimension. info, if not NULL,
+ * receives sum(nrhs) reports in instance order; the call then waits for
+ * `stream`. Returns the worst status as ovs_sign_apply. */
 int ovs_sign_apply_batched(int32_t n, const ovs_gauge_t* g, const void* const* x, void* const* y,
                            const int32_t* nrhs, const ovs_apply_opts* opts, ovs_apply_info* info, void* stream);
 

@@ -5,7 +5,7 @@ For a plane wave e^{i p.n} (p_nu = 2 pi k_nu / L_nu in space and
 p_4 = 2 pi (k_4 + 1/2) / L_t for the antiperiodic time direction), set
 p~_nu = p_nu for nu < 4 and p~_4 = p_4 - i mu. The forward hop contributes
 (1 - gamma_nu) e^{i p~_nu} and the backward hop (1 + gamma_nu) e^{-i p~_nu}
-(hop convention "baseline"), so
+(hop convention "minus_forward"), so
 
     D(p) = a + i sum_nu b_nu gamma_nu,
     a    = 1 - 2 kappa sum_nu cos p~_nu,   b_nu = 2 kappa sin p~_nu,

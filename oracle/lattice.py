@@ -12,11 +12,11 @@ Readings where the paper is silent:
   gamma4 = diag(1, 1, -1, -1);
 * boundary conditions: periodic in space, antiperiodic in time (a factor -1
   on every hop that wraps around in t);
-* hop convention: the default ``"baseline"`` puts (1 - gamma_nu) on the
+* hop convention: the default ``"minus_forward"`` puts (1 - gamma_nu) on the
   forward hop and (1 + gamma_nu) on the backward hop; ``"paper"`` is Eq. Dw as
   printed, (1 + gamma_j) forward and (1 - gamma_j) backward. The two are
-  related by D_paper = gamma5 D_baseline gamma5, so they share the spectrum
-  and sgn(H_paper) = gamma5 sgn(H_baseline) gamma5.
+  related by D_paper = gamma5 D_minus_forward gamma5, so they share the spectrum
+  and sgn(H_paper) = gamma5 sgn(H_minus_forward) gamma5.
 
 Index of a vector entry: (s*4 + spin)*3 + colour, s = ((t*Lz+z)*Ly+y)*Lx+x.
 """
@@ -73,7 +73,7 @@ def _hop_blocks(spin, links):
     return blk.reshape(v, 12, 12)
 
 
-def wilson_dirac(links, dims, mu, m_w, convention="baseline"):
+def wilson_dirac(links, dims, mu, m_w, convention="minus_forward"):
     """Sparse D_w(mu) (N x N, N = 12 V) built hop by hop from Eq. Dw."""
     dims = tuple(int(d) for d in dims)
     v = dims[0] * dims[1] * dims[2] * dims[3]
@@ -81,8 +81,8 @@ def wilson_dirac(links, dims, mu, m_w, convention="baseline"):
     kappa = kappa_of(m_w)
     gam = gamma_matrices()
     one = np.eye(4, dtype=np.complex128)
-    sign_fwd = -1.0 if convention == "baseline" else +1.0
-    if convention not in ("baseline", "paper"):
+    sign_fwd = -1.0 if convention == "minus_forward" else +1.0
+    if convention not in ("minus_forward", "paper"):
         raise ValueError("convention must be 'baseline' or 'paper'")
     sites = np.arange(v)
     rows_all, cols_all, vals_all = [], [], []
@@ -121,7 +121,7 @@ def wilson_dirac(links, dims, mu, m_w, convention="baseline"):
     return d
 
 
-def wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention="baseline"):
+def wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention="minus_forward"):
     """(D_w(mu) x) at the listed sites only, as an array (len(sites), 12).
 
     Each of the eight hops of Eq. Dw is summed directly for the requested
@@ -132,9 +132,9 @@ def wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention="baseline"):
     dims = tuple(int(d) for d in dims)
     lx, ly, lz, lt = dims
     sites = np.asarray(sites, dtype=np.int64)
-    if convention not in ("baseline", "paper"):
+    if convention not in ("minus_forward", "paper"):
         raise ValueError("convention must be 'baseline' or 'paper'")
-    sign_fwd = -1.0 if convention == "baseline" else +1.0
+    sign_fwd = -1.0 if convention == "minus_forward" else +1.0
     kappa = kappa_of(m_w)
     gam = gamma_matrices()
     one = np.eye(4, dtype=np.complex128)
@@ -163,7 +163,7 @@ def wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention="baseline"):
     return out.reshape(len(sites), 12)
 
 
-def hw_sites(links, dims, mu, m_w, x, sites, convention="baseline"):
+def hw_sites(links, dims, mu, m_w, x, sites, convention="minus_forward"):
     """(H_w(mu) x) = (gamma5 D_w(mu) x) at the listed sites (Sec. 2, Eq. Dov)."""
     d = wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention)
     return d * np.repeat(np.real(np.diag(gamma5())), 3)[None, :]
@@ -175,7 +175,7 @@ def gamma5_diag(v):
     return np.tile(np.repeat(g5, 3), v)
 
 
-def hw_operator(links, dims, mu, m_w, convention="baseline"):
+def hw_operator(links, dims, mu, m_w, convention="minus_forward"):
     """Sparse H_w(mu) = gamma5 D_w(mu) (Sec. 2, Eq. Dov)."""
     d = wilson_dirac(links, dims, mu, m_w, convention)
     v = d.shape[0] // 12

@@ -10,9 +10,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -242,10 +244,42 @@ static void free_kry(KryWork& k) {
 }
 
 static void drop_graphs(ovs_gauge_s* g) {
-    for (auto& e : g->graphs) cudaGraphExecDestroy(e.exec);
+    for (auto& e : g->graphs) cudaGraphDestroy(e.graph);
     g->graphs.clear();
     ++g->gen;
 }
+
+// Combined graphs of the batched form: one per set of instances (handle
+// uid and generation), right-hand-side counts and options; every instance's
+// recorded application is a child graph, so one launch runs them all.
+namespace {
+struct BatchEntry {
+    std::vector<unsigned long long> uids;
+    std::vector<unsigned> gens;
+    std::vector<int> nrhs;
+    int kmax, prec, every, flags;
+    double tol;
+    cudaGraphExec_t exec;
+};
+std::mutex g_batch_mu;
+std::vector<BatchEntry> g_batches;
+std::atomic<unsigned long long> g_next_uid{1};
+
+// Drop the combined graphs that contain handle uid (all of them if uid = 0
+// is never used: uids start at 1).
+void drop_batches_of(unsigned long long uid) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size();) {
+        const auto& u = g_batches[i].uids;
+        if (std::find(u.begin(), u.end(), uid) != u.end()) {
+            cudaGraphExecDestroy(g_batches[i].exec);
+            g_batches.erase(g_batches.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+}  // namespace
 
 void ovs::free_deflation(ovs_gauge_s* g) {
     drop_graphs(g);
@@ -361,6 +395,7 @@ static int new_handle(const int32_t dims[4], const double* links_host, int32_t p
     TRY(check_dims(dims));
     if (prec != OVS_F64 && prec != OVS_MIXED) return fail(OVS_EINVAL, "prec must be OVS_F64 or OVS_MIXED");
     ovs_gauge_s* g = new ovs_gauge_s();
+    g->uid = g_next_uid.fetch_add(1);
     for (int i = 0; i < 4; ++i) g->dims[i] = dims[i];
     g->geom = make_geom(dims);
     g->V = g->geom.V;
@@ -1255,7 +1290,7 @@ int ovs_get_krylov(ovs_gauge_t g, int32_t rhs, int32_t* k_out, double* V, double
 static int get_graph(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts, ovs_gauge_s::GraphEntry** out) {
     for (auto& e : g->graphs)
         if (e.gen == g->gen && e.nrhs == nrhs && e.kmax == opts->k_max && e.prec == opts->prec &&
-            e.every == opts->check_every && e.tol == opts->tol) {
+            e.every == opts->check_every && e.flags == opts->flags && e.tol == opts->tol) {
             *out = &e;
             return OVS_OK;
         }
@@ -1264,6 +1299,7 @@ static int get_graph(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts, ovs_g
     e.kmax = opts->k_max;
     e.prec = opts->prec;
     e.every = opts->check_every;
+    e.flags = opts->flags;
     e.tol = opts->tol;
     e.gen = g->gen;
     long long l0[OVS_PROF_NCLASS];
@@ -1289,9 +1325,7 @@ static int get_graph(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts, ovs_g
         return rc;
     }
     CK(ec);
-    const cudaError_t ei = cudaGraphInstantiate(&e.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    CK(ei);
+    e.graph = graph;
     g->graphs.push_back(e);
     *out = &g->graphs.back();
     return OVS_OK;
@@ -1310,44 +1344,90 @@ int ovs_sign_apply_batched(int32_t n, const ovs_gauge_t* gs, const void* const* 
     }
     cudaStream_t st = (cudaStream_t)stream;
     const int tp = tprec_of(opts->prec);
-    cudaEvent_t fork = nullptr;
-    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    cudaError_t e = cudaEventRecord(fork, st);
-    bool any_host = false;
-    int rc = OVS_OK;
-    for (int i = 0; i < n && e == cudaSuccess && rc == OVS_OK; ++i) {
+    std::vector<ovs_gauge_s::GraphEntry*> ges(n);
+    for (int i = 0; i < n; ++i) {
         ovs_gauge_s* g = gs[i];
-        if ((rc = ensure_vec(g, nrhs[i], tp)) < 0) break;
-        if ((rc = ensure_kry(g, nrhs[i], opts->k_max, tp)) < 0) break;
+        TRY(ensure_vec(g, nrhs[i], tp));
+        TRY(ensure_kry(g, nrhs[i], opts->k_max, tp));
         // choose the stencil shape now: the recorded application cannot time it
         stencil_shape(g, tp, nrhs[i], g->vw.xint, field_bytes(g->N, tp), g->vw.wvec, field_bytes(g->N, tp), st);
-        if (!g->istream) e = cudaStreamCreateWithFlags(&g->istream, cudaStreamNonBlocking);
-        if (e == cudaSuccess && !g->ev_join) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
-        if (e != cudaSuccess) break;
-        ovs_gauge_s::GraphEntry* ge = nullptr;
-        if ((rc = get_graph(g, nrhs[i], opts, &ge)) < 0) break;
-        const size_t bytes = field_bytes(g->N, PREC_F64) * nrhs[i];
-        const bool xdev = is_device_ptr(x[i]), ydev = is_device_ptr(y[i]);
-        any_host = any_host || !ydev;
-        e = cudaStreamWaitEvent(g->istream, fork, 0);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(g->vw.sx, x[i], bytes, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                g->istream);
-        if (e == cudaSuccess) e = cudaGraphLaunch(ge->exec, g->istream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(y[i], g->vw.sy, bytes, ydev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                g->istream);
-        if (e == cudaSuccess) e = cudaEventRecord(g->ev_join, g->istream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g->ev_join, 0);
-        for (int c = 0; c < OVS_PROF_NCLASS; ++c) {
-            g->prof_launches[c] += ge->launches[c];
-            g->prof_bytes[c] += ge->bytes[c];
-        }
-        remember_apply(g, nrhs[i], opts, g->istream);
+        if (!g->istream) CK(cudaStreamCreateWithFlags(&g->istream, cudaStreamNonBlocking));
+        TRY(get_graph(g, nrhs[i], opts, &ges[i]));
     }
-    cudaEventDestroy(fork);
-    if (rc < 0) return rc;
-    CK(e);
+    // the combined graph of these instances (built once, then replayed)
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        for (auto it = g_batches.begin(); it != g_batches.end() && !exec; ++it) {
+            if ((int)it->uids.size() != n || it->kmax != opts->k_max || it->prec != opts->prec ||
+                it->every != opts->check_every || it->flags != opts->flags || it->tol != opts->tol)
+                continue;
+            bool same = true;
+            for (int i = 0; i < n && same; ++i)
+                same = it->uids[i] == gs[i]->uid && it->gens[i] == gs[i]->gen && it->nrhs[i] == nrhs[i];
+            if (same) exec = it->exec;
+        }
+        if (!exec) {
+            // entries of these handles at older generations can never match again
+            for (size_t q = 0; q < g_batches.size();) {
+                bool stale = false;
+                for (int i = 0; i < n && !stale; ++i)
+                    for (size_t u = 0; u < g_batches[q].uids.size(); ++u)
+                        stale = stale || (g_batches[q].uids[u] == gs[i]->uid && g_batches[q].gens[u] != gs[i]->gen);
+                if (stale) {
+                    cudaGraphExecDestroy(g_batches[q].exec);
+                    g_batches.erase(g_batches.begin() + q);
+                } else {
+                    ++q;
+                }
+            }
+            cudaGraph_t parent = nullptr;
+            CK(cudaGraphCreate(&parent, 0));
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                cudaGraphNode_t node;
+                e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, ges[i]->graph);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, parent, 0);
+            cudaGraphDestroy(parent);
+            CK(e);
+            BatchEntry be;
+            be.kmax = opts->k_max;
+            be.prec = opts->prec;
+            be.every = opts->check_every;
+            be.flags = opts->flags;
+            be.tol = opts->tol;
+            be.exec = exec;
+            for (int i = 0; i < n; ++i) {
+                be.uids.push_back(gs[i]->uid);
+                be.gens.push_back(gs[i]->gen);
+                be.nrhs.push_back(nrhs[i]);
+            }
+            g_batches.push_back(be);
+        }
+    }
+    // inputs into the instances' staging buffers, one launch for all
+    // instances, outputs back; all on the caller's stream
+    bool any_host = false;
+    for (int i = 0; i < n; ++i) {
+        ovs_gauge_s* g = gs[i];
+        const size_t bytes = field_bytes(g->N, PREC_F64) * nrhs[i];
+        const bool xdev = is_device_ptr(x[i]);
+        CK(cudaMemcpyAsync(g->vw.sx, x[i], bytes, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaGraphLaunch(exec, st));
+    for (int i = 0; i < n; ++i) {
+        ovs_gauge_s* g = gs[i];
+        const size_t bytes = field_bytes(g->N, PREC_F64) * nrhs[i];
+        const bool ydev = is_device_ptr(y[i]);
+        any_host = any_host || !ydev;
+        CK(cudaMemcpyAsync(y[i], g->vw.sy, bytes, ydev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        for (int c = 0; c < OVS_PROF_NCLASS; ++c) {
+            g->prof_launches[c] += ges[i]->launches[c];
+            g->prof_bytes[c] += ges[i]->bytes[c];
+        }
+        remember_apply(g, nrhs[i], opts, st);
+    }
     if (info) {
         int worst = OVS_OK, off = 0;
         for (int i = 0; i < n; ++i) {
@@ -1479,6 +1559,7 @@ int ovs_profile_read(ovs_gauge_t g, double* ms, int64_t* launches, double* bytes
 void ovs_destroy(ovs_gauge_t g) {
     if (!g) return;
     prof_flush(g);
+    drop_batches_of(g->uid);
     drop_graphs(g);
     if (g->ev_join) cudaEventDestroy(g->ev_join);
     if (g->istream) cudaStreamDestroy(g->istream);

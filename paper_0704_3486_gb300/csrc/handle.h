@@ -93,15 +93,16 @@ struct ovs_gauge_s {
     cudaStream_t prof_stream = nullptr;
     // batched form: recorded applications (CUDA graphs) and a private stream
     struct GraphEntry {
-        int nrhs, kmax, prec, every;
+        int nrhs, kmax, prec, every, flags;
         double tol;
         unsigned gen;
-        cudaGraphExec_t exec;
+        cudaGraph_t graph;  // the recorded application (a child of the batched form's graphs)
         long long launches[OVS_PROF_NCLASS];
         double bytes[OVS_PROF_NCLASS];
     };
     std::vector<GraphEntry> graphs;
     unsigned gen = 1;  // bumped whenever buffers, mu or the deflation basis change
+    unsigned long long uid = 0;  // unique over the process (keys of the combined batched graphs)
     bool capturing = false;
     cudaStream_t istream = nullptr;
     cudaEvent_t ev_join = nullptr;

@@ -221,16 +221,26 @@ __global__ void __launch_bounds__(NT) k_newton(const double2* __restrict__ H, lo
 // Cluster form: one matrix per cluster of ncl CTAs (one per SM; ncl is the
 // launch's cluster size). CTA c holds the column block [c*W, c*W + W) of the
 // matrix being inverted in shared memory (W = ceil(n/ncl)); the iterate S
-// stays in global memory (each CTA
-// touches only its own columns). Gauss-Jordan step p: the owner of column p
-// picks the pivot and publishes the pivot index and the (row-swapped)
-// column p in its shared memory, double-buffered by the parity of p; one
-// cluster barrier makes them visible; every CTA copies them through
-// distributed shared memory, swaps rows p and pivot in its block, and
-// eliminates. After the last step the row interchanges are undone as a
-// column permutation read from the owners' blocks while S <- (S + S^-1)/2 is
-// formed, and the norms of the change are summed over the cluster.
+// stays in global memory (each CTA touches only its own columns).
+//
+// Gauss-Jordan with the pivots taken in panels of up to bw consecutive
+// columns, all inside one CTA's block (the panel's owner):
+//  A. the owner runs the panel's pivots on the panel columns alone: for each
+//     pivot p it searches the pivot row, publishes p's pivot row and its
+//     (row-swapped) column p, and eliminates on the panel columns;
+//  B. one cluster barrier per panel makes the panel visible; every CTA
+//     copies it through distributed shared memory and applies the panel's
+//     pivots, in order, to all its other columns (swap rows p and pivot,
+//     scale the pivot row, eliminate).
+// Every column therefore receives the same operations in the same order as
+// with one barrier per pivot, so the result is the same bit for bit; the
+// cluster barriers and the waits for the pivot search fall by the panel
+// width. The published panels are double-buffered by the parity of the
+// panel index. After the last panel the row interchanges are undone as a
+// column permutation read from the owners' blocks while S <- (S + S^-1)/2
+// is formed, and the norms of the change are summed over the cluster.
 constexpr int NTC = 512;
+constexpr int kMaxPanel = 8;
 constexpr int kClusterSizes[] = {8, 7, 6, 5, 4};  // candidates, largest first
 
 __device__ __forceinline__ double cl_block_sum(double v, double* sh) {
@@ -245,19 +255,76 @@ __device__ __forceinline__ double cl_block_sum(double v, double* sh) {
     return s;
 }
 
+// One Gauss-Jordan pivot p on the local columns jj in [jb, je) of T (row
+// stride W), skipping the local columns in [sb, se): rows p and piv
+// swapped, the pivot row scaled by inv, every other row eliminated with
+// the pivot column col (after the swap); column p itself, where present,
+// becomes -col * inv with inv on the diagonal. All threads of the CTA call
+// it with the same arguments.
+__device__ __forceinline__ void gj_apply(cd* T, int W, int n, int c0, int jb, int je, int sb, int se, int p,
+                                         int piv, const cd* col, cd inv, cd* rowp) {
+    const int tid = threadIdx.x;
+    const int w = je - jb;
+    if (w <= 0) return;
+    if (piv != p) {
+        for (int q = tid; q < w; q += NTC) {
+            const int jj = jb + q;
+            if (jj >= sb && jj < se) continue;
+            const cd t = T[(size_t)p * W + jj];
+            T[(size_t)p * W + jj] = T[(size_t)piv * W + jj];
+            T[(size_t)piv * W + jj] = t;
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < w; q += NTC) {
+        const int jj = jb + q;
+        rowp[jj] = (c0 + jj == p) ? inv : cmul(T[(size_t)p * W + jj], inv);
+    }
+    __syncthreads();
+    // elimination mapping: a fixed column and every erows-th row
+    const int erows = NTC / w;
+    const int ej = tid % w, ei = tid / w;
+    if (ei < erows) {
+        const int jj = jb + ej;
+        if (!(jj >= sb && jj < se)) {
+            const cd gg = rowp[jj];
+            const bool pcol = (c0 + jj == p);
+            for (int i = ei; i < n; i += erows) {
+                if (i == p) {
+                    T[(size_t)i * W + jj] = gg;
+                } else if (pcol) {
+                    T[(size_t)i * W + jj] = -cmul(col[i], inv);
+                } else {
+                    cd v = T[(size_t)i * W + jj];
+                    const cd f = col[i];
+                    v.re = fma(-f.re, gg.re, v.re);
+                    v.re = fma(f.im, gg.im, v.re);
+                    v.im = fma(-f.re, gg.im, v.im);
+                    v.im = fma(-f.im, gg.re, v.im);
+                    T[(size_t)i * W + jj] = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(NTC)
     k_newton_cluster(const double2* __restrict__ H, long long h_rhs_stride, int ldh, const int* __restrict__ k_used,
                      const double* __restrict__ beta, double2* __restrict__ coeff, long long coeff_stride,
-                     double2* __restrict__ work, int kmax, int kc, int* __restrict__ iters, int* __restrict__ status,
-                     const int* __restrict__ active, int n_fixed) {
+                     double2* __restrict__ work, int kmax, int kc, int bw, int* __restrict__ iters,
+                     int* __restrict__ status, const int* __restrict__ active, int n_fixed) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ unsigned char smem_raw[];
-    __shared__ int s_piv[2], s_ok[2];
-    __shared__ double2 s_inv;
+    __shared__ int s_pidx[2][kMaxPanel], s_ok[2];
+    __shared__ double2 s_pinv[2][kMaxPanel];
+    __shared__ int s_piv;
     __shared__ double s_part[2];
     __shared__ double s_red[NTC / 32];
     __shared__ double s_bv[NTC / 32];
     __shared__ int s_bi[NTC / 32];
+    __shared__ cd s_inv_l[kMaxPanel];
+    __shared__ int s_piv_l[kMaxPanel];
     const int c = (int)cl.block_rank();
     const int ncl = (int)cl.num_blocks();
     const int r = blockIdx.x / ncl;
@@ -267,9 +334,9 @@ __global__ void __launch_bounds__(NTC)
     // shared-memory layout for matrices of order <= kc (kc <= kmax)
     const int Wmax = (kc + ncl - 1) / ncl;
     cd* T = reinterpret_cast<cd*>(smem_raw);          // [kc][Wmax]
-    cd* colp = T + (size_t)kc * Wmax;                 // [2][kc] published pivot columns
-    cd* colL = colp + 2 * (size_t)kc;                 // [kc] local copy
-    cd* rowp = colL + kc;                             // [Wmax]
+    cd* pub = T + (size_t)kc * Wmax;                  // [2][bw][kc] published panel columns
+    cd* colL = pub + 2 * (size_t)bw * kc;             // [bw][kc] local copy of the panel
+    cd* rowp = colL + (size_t)bw * kc;                // [Wmax]
     int* perm = reinterpret_cast<int*>(rowp + Wmax);  // [kc]
     int* srcc = perm + kc;                            // [kc]
     double2* cr = coeff + r * coeff_stride;
@@ -283,10 +350,6 @@ __global__ void __launch_bounds__(NTC)
     const int W = (n + ncl - 1) / ncl;
     const int c0 = c * W;
     const int w = max(0, min(n, c0 + W) - c0);
-    // elimination mapping: a fixed column ej and every erows-th row from ei
-    // (threads beyond erows * W idle there)
-    const int erows = NTC / W;
-    const int ej = tid % W, ei = tid / W;
     cd* S = reinterpret_cast<cd*>(work) + (size_t)r * 2 * kmax * kmax;  // row-major n x n
     const double2* Hr = H + r * h_rhs_stride;
     for (int idx = tid; idx < n * w; idx += NTC) {
@@ -302,86 +365,85 @@ __global__ void __launch_bounds__(NTC)
         }
         __syncthreads();
         bool ok = true;
-        for (int p = 0; p < n; ++p) {
-            const int owner = p / W, buf = p & 1;
+        int panel = 0;
+        for (int p0 = 0; p0 < n; ++panel) {
+            const int owner = p0 / W;
+            const int p1 = min(min(p0 + bw, (owner + 1) * W), n);
+            const int cnt = p1 - p0;
+            const int buf = panel & 1;
             if (c == owner) {
-                const int jl = p - c0;
-                double best = -1.0;
-                int bi = p;
-                for (int i = p + tid; i < n; i += NTC) {
-                    const cd a = T[(size_t)i * W + jl];
-                    const double v = a.re * a.re + a.im * a.im;
-                    if (v > best) { best = v; bi = i; }
-                }
-                for (int off = 16; off > 0; off >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, best, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-                }
-                if ((tid & 31) == 0) { s_bv[tid >> 5] = best; s_bi[tid >> 5] = bi; }
+                // A. the panel's pivots on the panel columns [p0 - c0, p1 - c0)
+                if (tid == 0) s_ok[buf] = 1;
                 __syncthreads();
-                if (tid == 0) {
-                    double b = s_bv[0];
-                    int ib = s_bi[0];
-                    for (int q = 1; q < NTC / 32; ++q)
-                        if (s_bv[q] > b || (s_bv[q] == b && s_bi[q] < ib)) { b = s_bv[q]; ib = s_bi[q]; }
-                    s_piv[buf] = ib;
-                    s_ok[buf] = (b > 0.0 && isfinite(b)) ? 1 : 0;
-                }
-                __syncthreads();
-                const int piv = s_piv[buf];
-                for (int i = tid; i < n; i += NTC) {
-                    const int si = (i == p) ? piv : (i == piv ? p : i);
-                    colp[(size_t)buf * kc + i] = T[(size_t)si * W + jl];
+                for (int p = p0; p < p1; ++p) {
+                    const int jl = p - c0, k = p - p0;
+                    double best = -1.0;
+                    int bi = p;
+                    for (int i = p + tid; i < n; i += NTC) {
+                        const cd a = T[(size_t)i * W + jl];
+                        const double v = a.re * a.re + a.im * a.im;
+                        if (v > best) { best = v; bi = i; }
+                    }
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                    }
+                    if ((tid & 31) == 0) { s_bv[tid >> 5] = best; s_bi[tid >> 5] = bi; }
+                    __syncthreads();
+                    if (tid == 0) {
+                        double b = s_bv[0];
+                        int ib = s_bi[0];
+                        for (int q = 1; q < NTC / 32; ++q)
+                            if (s_bv[q] > b || (s_bv[q] == b && s_bi[q] < ib)) { b = s_bv[q]; ib = s_bi[q]; }
+                        s_piv = ib;
+                        s_pidx[buf][k] = ib;
+                        if (!(b > 0.0 && isfinite(b))) s_ok[buf] = 0;
+                    }
+                    __syncthreads();
+                    if (!s_ok[buf]) break;  // uniform over the CTA
+                    const int piv = s_piv;
+                    cd* pc = pub + ((size_t)buf * bw + k) * kc;
+                    for (int i = tid; i < n; i += NTC) {
+                        const int si = (i == p) ? piv : (i == piv ? p : i);
+                        pc[i] = T[(size_t)si * W + jl];
+                    }
+                    __syncthreads();
+                    if (tid == 0) {  // the pivot's inverse, once per panel column
+                        const cd a = pc[p];
+                        const double den = a.re * a.re + a.im * a.im;
+                        s_pinv[buf][k] = make_double2(a.re / den, -a.im / den);
+                    }
+                    __syncthreads();
+                    const cd inv = {s_pinv[buf][k].x, s_pinv[buf][k].y};
+                    gj_apply(T, W, n, c0, p0 - c0, p1 - c0, 0, 0, p, piv, pc, inv, rowp);
                 }
             }
             cl.sync();
-            const int piv = *cl.map_shared_rank(&s_piv[buf], owner);
-            const int okp = *cl.map_shared_rank(&s_ok[buf], owner);
-            if (!okp) {
+            // B. the panel's pivots on every other column of this CTA
+            if (!*cl.map_shared_rank(&s_ok[buf], owner)) {
                 ok = false;
-                break;
+                break;  // uniform over the cluster
             }
-            const cd* rcol = cl.map_shared_rank(colp + (size_t)buf * kc, owner);
-            for (int i = tid; i < n; i += NTC) colL[i] = rcol[i];
-            if (tid == 0) {  // the pivot's inverse, once per block
-                perm[p] = piv;
-                const cd a = rcol[p];
-                const double den = a.re * a.re + a.im * a.im;
-                s_inv = make_double2(a.re / den, -a.im / den);
-            }
-            if (piv != p) {
-                for (int jj = tid; jj < w; jj += NTC) {
-                    const cd t = T[(size_t)p * W + jj];
-                    T[(size_t)p * W + jj] = T[(size_t)piv * W + jj];
-                    T[(size_t)piv * W + jj] = t;
+            {
+                const cd* rpub = cl.map_shared_rank(pub + (size_t)buf * bw * kc, owner);
+                for (int idx = tid; idx < cnt * n; idx += NTC) {
+                    const int k = idx / n, i = idx - k * n;
+                    colL[(size_t)k * kc + i] = rpub[(size_t)k * kc + i];
+                }
+                if (tid < cnt) {
+                    const int* rp = cl.map_shared_rank(&s_pidx[buf][0], owner);
+                    const double2* ri = cl.map_shared_rank(&s_pinv[buf][0], owner);
+                    s_piv_l[tid] = rp[tid];
+                    s_inv_l[tid] = {ri[tid].x, ri[tid].y};
+                    perm[p0 + tid] = rp[tid];
                 }
             }
             __syncthreads();
-            const cd inv = {s_inv.x, s_inv.y};
-            for (int jj = tid; jj < w; jj += NTC)
-                rowp[jj] = (c0 + jj == p) ? inv : cmul(T[(size_t)p * W + jj], inv);
-            __syncthreads();
-            if (ej < w && ei < erows) {  // this thread's column ej, rows ei, ei + erows, ...
-                const cd gg = rowp[ej];
-                const bool pcol = (c0 + ej == p);
-                for (int i = ei; i < n; i += erows) {
-                    if (i == p) {
-                        T[(size_t)i * W + ej] = gg;
-                    } else if (pcol) {
-                        T[(size_t)i * W + ej] = -cmul(colL[i], inv);
-                    } else {
-                        cd v = T[(size_t)i * W + ej];
-                        const cd f = colL[i];
-                        v.re = fma(-f.re, gg.re, v.re);
-                        v.re = fma(f.im, gg.im, v.re);
-                        v.im = fma(-f.re, gg.im, v.im);
-                        v.im = fma(-f.im, gg.re, v.im);
-                        T[(size_t)i * W + ej] = v;
-                    }
-                }
-            }
-            __syncthreads();
+            const int sb = (c == owner) ? p0 - c0 : 0, se = (c == owner) ? p1 - c0 : 0;
+            for (int k = 0; k < cnt; ++k)
+                gj_apply(T, W, n, c0, 0, w, sb, se, p0 + k, s_piv_l[k], colL + (size_t)k * kc, s_inv_l[k], rowp);
+            p0 = p1;
         }
         if (!ok) {
             cl.sync();  // the owner's flag was read remotely: no block leaves before all have read it
@@ -578,12 +640,20 @@ cudaError_t launch_harmonic(void* H, long long h_rhs_stride, int ldh, const int*
     return cudaGetLastError();
 }
 
-static size_t cluster_smem(int kmax, int ncl) {
+static size_t cluster_smem(int kmax, int ncl, int bw) {
     const int Wmax = (kmax + ncl - 1) / ncl;
-    return ((size_t)kmax * Wmax + 3 * (size_t)kmax + Wmax) * sizeof(cd) + 2 * (size_t)kmax * sizeof(int);
+    return ((size_t)kmax * Wmax + 3 * (size_t)bw * kmax + Wmax) * sizeof(cd) + 2 * (size_t)kmax * sizeof(int);
 }
 
 constexpr size_t kClusterSmemMax = 220 * 1024;
+
+// Widest panel (8, 4, 2 or 1 columns) whose buffers fit next to the blocks
+// of a cluster of ncl CTAs; 0 if not even one column fits.
+static int panel_width(int kmax, int ncl) {
+    for (int bw = kMaxPanel; bw >= 1; bw /= 2)
+        if (cluster_smem(kmax, ncl, bw) <= kClusterSmemMax) return bw;
+    return 0;
+}
 
 // Cluster size for nrhs matrices of order <= kmax: the candidate with the
 // fewest waves per SM of a cluster (waves / ncl, the FP64 work per SM being
@@ -606,8 +676,9 @@ static int pick_cluster(int kmax, int nrhs) {
     int best = 0;
     double best_cost = 0.0;
     for (int ncl : kClusterSizes) {
-        const size_t need = cluster_smem(kmax, ncl);
-        if (need > kClusterSmemMax) continue;
+        const int bw = panel_width(kmax, ncl);
+        if (bw == 0) continue;
+        const size_t need = cluster_smem(kmax, ncl, bw);
         auto key = std::make_tuple(dev, ncl, need);
         auto it = resident.find(key);
         if (it == resident.end()) {
@@ -656,12 +727,13 @@ cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const 
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(nrhs * ncl);
         cfg.blockDim = dim3(NTC);
-        cfg.dynamicSmemBytes = cluster_smem(kc, ncl);
+        const int bw = panel_width(kc, ncl);
+        cfg.dynamicSmemBytes = cluster_smem(kc, ncl, bw);
         cfg.stream = st;
         cfg.attrs = at;
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k_newton_cluster, (const double2*)H, h_rhs_stride, ldh, k_used, beta,
-                                  (double2*)coeff, coeff_stride, (double2*)work, kmax, kc, iters, status, active,
+                                  (double2*)coeff, coeff_stride, (double2*)work, kmax, kc, bw, iters, status, active,
                                   n_fixed);
     }
     const size_t smem = (size_t)kmax * 2 * sizeof(cd) + (size_t)kmax * sizeof(int);

@@ -38,7 +38,10 @@ std::mutex g_scratch_mutex;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the array on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached for the life of the process.
+// A cudaDeviceReset destroys the context that holds the array: the cached
+// address is then stale, so a caller that resets a device must not call
+// this entry point on it afterwards.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -77,7 +80,15 @@ extern "C" int ovs_matvec_noalloc(ovs_gauge_t g, int32_t op, const void* x, void
         return lib_fail(OVS_EINVAL,
                         "ovs_matvec_noalloc: nrhs * N exceeds the fixed work array (8 MiB per field: "
                         "nrhs * N <= 524288 for OVS_F64, <= 1048576 for OVS_MIXED); use ovs_matvec");
-    // host buffers would need staging memory: only device (or managed) pointers
+    // host buffers would need staging memory: only device (or managed)
+    // pointers, on the current device, which must be the handle's (its links
+    // and the array used below live there)
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return lib_fail(OVS_ECUDA, "ovs_matvec_noalloc: no current device");
+    }
+    if (cur != g->device) return lib_fail(OVS_EINVAL, "ovs_matvec_noalloc: the current device is not the handle's");
     for (const void* p : {x, (const void*)y}) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
@@ -85,6 +96,8 @@ extern "C" int ovs_matvec_noalloc(ovs_gauge_t g, int32_t op, const void* x, void
             cudaGetLastError();
             return lib_fail(OVS_EINVAL, "ovs_matvec_noalloc: x and y must be device pointers");
         }
+        if (a.type == cudaMemoryTypeDevice && a.device != cur)
+            return lib_fail(OVS_EINVAL, "ovs_matvec_noalloc: x and y must be on the current device");
     }
     void* base = nullptr;
     cudaError_t e = scratch_address(&base);
@@ -94,15 +107,20 @@ extern "C" int ovs_matvec_noalloc(ovs_gauge_t g, int32_t op, const void* x, void
     cudaStream_t st = (cudaStream_t)stream;
     const long long N = g->N;
     const void* L = tp == PREC_F64 ? g->links64 : g->links32;
+    // the stencil shape already chosen for (precision, nrhs) on this handle,
+    // if any (no tuning here: it would time launches on the caller's stream)
+    StencilShape sh{};
+    const auto tuned = g->tuned.find(std::make_pair(tp, (int)nrhs));
+    if (tuned != g->tuned.end()) sh = tuned->second.best;
     e = launch_to_internal(tp, x, N, f0, fb, (int)g->V, nrhs, st);
     if (e == cudaSuccess) {
         if (op == OVS_OP_HW2) {
-            e = launch_wilson(tp, true, L, f0, fb, f1, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st);
+            e = launch_wilson(tp, true, L, f0, fb, f1, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st, sh);
             if (e == cudaSuccess)
-                e = launch_wilson(tp, true, L, f1, fb, f0, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st);
+                e = launch_wilson(tp, true, L, f1, fb, f0, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st, sh);
             if (e == cudaSuccess) e = launch_to_canonical(tp, f0, fb, y, N, (int)g->V, nrhs, st);
         } else {
-            e = launch_wilson(tp, op == OVS_OP_HW, L, f0, fb, f1, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st);
+            e = launch_wilson(tp, op == OVS_OP_HW, L, f0, fb, f1, fb, g->geom, nrhs, g->kappa, g->mu, nullptr, st, sh);
             if (e == cudaSuccess) e = launch_to_canonical(tp, f1, fb, y, N, (int)g->V, nrhs, st);
         }
     }

@@ -195,3 +195,21 @@ def test_batched_instance_recipe(gpu):
         assert len(set(ks)) > 1  # uneven Krylov depths within the batch
     for g in gs:
         g.destroy()
+
+
+def test_batched_single_graph_survives_handle_churn(gpu):
+    """The combined graph of a batch is keyed by the handles' unique ids: a
+    handle destroyed and a new one created (possibly at the same address)
+    never replays a stale combined graph; results follow the new handle."""
+    specs = [((4, 4, 4, 4), 7, 0.5, 0.2, 2, 0), ((2, 4, 4, 4), 8, 0.6, 0.1, 1, 0)]
+    for rep in range(3):
+        inst = [_instance(gpu, dims, seed + rep, eps, mu, nrhs, m) for (dims, seed, eps, mu, nrhs, m) in specs]
+        gs = [i[0] for i in inst]
+        xs = [torch.from_numpy(i[2]).cuda() for i in inst]
+        ys = [torch.empty_like(x) for x in xs]
+        gpu.sign_apply_batched(gs, xs, ys, 30, prec=gpu.F64)
+        for (g, h, x, _), yd in zip(inst, ys):
+            ref, _ = arnoldi.arnoldi_sign(lambda q: h @ q, x[0], 30)
+            assert rel(yd.cpu().numpy()[0], ref) < 1e-12, rep
+        for g in gs:
+            g.destroy()

@@ -72,7 +72,7 @@ def test_sampled_sites_match_sparse_operator():
     v = int(np.prod(dims))
     u = synth.gauge_links(dims, 7, 0.6)
     x = synth.gaussian_vectors(12 * v, 1, 14)[0]
-    for conv in ("baseline", "paper"):
+    for conv in ("minus_forward", "paper"):
         h = lattice.hw_operator(u, dims, MU, MW, conv)
         got = lattice.hw_sites(u, dims, MU, MW, x, np.arange(v), conv)
         assert np.abs(got.ravel() - h @ x).max() < 1e-13
@@ -128,7 +128,7 @@ def test_hop_conventions_related_by_gamma5():
     """Eq. Dw as printed vs the adopted convention: D_p = g5 D_b g5."""
     dims = (2, 2, 2, 4)
     u = synth.gauge_links(dims, 2, 0.6)
-    db = lattice.wilson_dirac(u, dims, MU, MW, "baseline").toarray()
+    db = lattice.wilson_dirac(u, dims, MU, MW, "minus_forward").toarray()
     dp = lattice.wilson_dirac(u, dims, MU, MW, "paper").toarray()
     g5 = np.diag(lattice.gamma5_diag(32))
     assert np.abs(dp - g5 @ db @ g5).max() < 1e-15
