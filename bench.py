@@ -53,12 +53,14 @@ def parse_args():
     p.add_argument("--no-long-ref", action="store_true", help="skip the FP64 k=790 reference of right-hand side 0")
     p.add_argument("--stencil-shape", type=int, nargs=3, default=None, metavar=("RT", "SITES", "RB"),
                    help="pin the stencil launch shape of the mixed form instead of autotuning it")
-    p.add_argument("--workload", choices=["single", "batched"], default="single",
+    p.add_argument("--workload", choices=["single", "batched", "overlap-solve"], default="single",
                    help="batched: the multi-instance recipe (32 instances of 4^4/6^4/8^4, m = 20 each, "
                         "per-vector convergence stop) in one ovs_sign_apply_batched call; its own JSON line")
     p.add_argument("--instances", type=int, default=32)
     p.add_argument("--full-application", action="store_true",
                    help="with --impl reference: time one complete oracle application instead of samples")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the harmonic / D_ov / Schur sub-measurements of the default line")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched multi-instance sub-measurement of the default line")
     return p.parse_args()
@@ -184,13 +186,16 @@ class CpuSample:
 
     Sample: one right-hand side of the full lattice; the oracle's LR
     deflation with m random (biorthonormalised) vectors and its CGS2
-    Arnoldi run for k_sample steps. The matvec and Gram-Schmidt costs are
-    measured separately and scaled to k steps as t = t0 + k t_mv +
-    c k(k+1)/2 (CGS2 sweeps grow linearly with the step), the Newton cost
-    as (k / k_sample)^3. The operator is built once (not timed).
+    Arnoldi run for k_sample steps. The wall time of each Arnoldi step j
+    (matvec plus the Gram-Schmidt passes over the j previous vectors, read
+    off the times of successive matvec calls) is fitted as a + c j and summed
+    to k steps; the projection before the first step is timed as it is; the
+    Newton sign is timed on a k x k matrix; the recombination y = V_k c
+    (one pass over V_k) is counted as a quarter of the Gram-Schmidt time of
+    step k. The operator is built once (not timed).
     """
 
-    def __init__(self, w, k_sample=8):
+    def __init__(self, w, k_sample=16):
         import numpy as np
 
         import synth
@@ -204,44 +209,56 @@ class CpuSample:
         self.r = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
         self.l = (rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))) / np.sqrt(n) if m else None
         self.lam = rng.standard_normal(m) + 0.5j * rng.standard_normal(m) if m else None
+        self.t_newton = None
+
+    def newton_time(self):
+        """Roberts' iteration on a k x k matrix with eigenvalues off the
+        imaginary axis (the cost depends on k and the iteration count only)."""
+        import numpy as np
+
+        from oracle import newton
+        if self.t_newton is None:
+            k = self.w["k"]
+            rng = np.random.default_rng(7)
+            d = rng.uniform(0.05, 2.0, k) * rng.choice([-1.0, 1.0], k)
+            a = np.triu(0.05 * (rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))), -1)
+            a[np.diag_indices(k)] = d
+            t0 = time.perf_counter()
+            newton.roberts_sign(a)
+            self.t_newton = time.perf_counter() - t0
+        return self.t_newton
 
     def run(self, seed_offset=0):
         """One sample. Returns (modelled seconds per application, measured
         seconds of the sample, description)."""
+        import numpy as np
+
         import synth
-        from oracle import deflation, newton
+        from oracle import deflation
 
         w, h, ks, k, m = self.w, self.h, self.ks, self.w["k"], self.w["m"]
         x = synth.gaussian_vectors(w["N"], 1, w["src_seed"] + seed_offset)[0]
-        t_mv = [0.0]
+        stamps = []
 
         def mv(v):
-            t = time.perf_counter()
-            out = h @ v
-            t_mv[0] += time.perf_counter() - t
-            return out
+            stamps.append(time.perf_counter())
+            return h @ v
 
         t_start = time.perf_counter()
-        t0 = time.perf_counter()
-        _, info = deflation.lr_sign_apply(mv, x, self.r, self.l, self.lam, ks)
-        total = time.perf_counter() - t0
-        tn = time.perf_counter()
-        newton.roberts_sign(info["H"][:ks, :ks])
-        t_newton = time.perf_counter() - tn
-        per_mv = t_mv[0] / ks
-        t_cgs = max(total - t_mv[0] - t_newton, 0.0)
-        # deflation projection: two sweeps of m vectors plus biorthonormalisation,
-        # measured apart from the Arnoldi loop by a second call with k = 1
-        t1 = time.perf_counter()
-        deflation.lr_sign_apply(lambda v: h @ v, x, self.r, self.l, self.lam, 1)
-        t_setup = time.perf_counter() - t1 - per_mv
+        deflation.lr_sign_apply(mv, x, self.r, self.l, self.lam, ks)
         t_sample = time.perf_counter() - t_start
-        t_cgs_loop = max(t_cgs - t_setup, 0.0)
-        c = t_cgs_loop / (ks * (ks + 1) / 2)
-        t_app = t_setup + k * per_mv + c * k * (k + 1) / 2 + t_newton * (k / ks) ** 3
-        desc = (f"1 RHS of the full lattice: LR projection (m={m}) + {ks} of {k} CGS2 Arnoldi steps "
-                f"timed ({total:.1f} s), the application's time MODELLED from it as t0 + k*t_mv + c*k(k+1)/2 "
-                f"(t_mv={per_mv:.3f} s, c={c:.2e} s); numpy/scipy FP64")
+        t_proj = stamps[0] - t_start
+        steps = np.diff(np.asarray(stamps))  # step j (j = 0 .. ks-2) lasted steps[j]
+        j = np.arange(len(steps))
+        c, a = np.polyfit(j, steps, 1)
+        c = max(c, 0.0)
+        t_arnoldi = k * a + c * k * (k - 1) / 2
+        t_recomb = 0.25 * c * k
+        t_app = t_proj + t_arnoldi + self.newton_time() + t_recomb
+        desc = (f"1 RHS of the full lattice: LR projection (m={m}) + {ks} of {k} CGS2 Arnoldi steps timed "
+                f"({t_sample:.1f} s); the application's time MODELLED from it: step j lasts a + c j "
+                f"(a={a:.3f} s, c={c:.2e} s, fitted), summed to k, plus the projection, a k x k Newton sign "
+                f"({self.newton_time():.2f} s) and the recombination; numpy/scipy FP64")
         return t_app, t_sample, desc
 
 
@@ -431,12 +448,67 @@ def run_ours(args, w, world, rank, local):
                        "status": ovs.STATUS.get(status, status)},
         "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
     }
+    if not args.no_variants:
+        out["variants"] = run_variants(ovs, g, x, y, k, stream, w)
     tuned = ovs.stencil_tuning(g, ovs.MIXED, w["nrhs"])
     if tuned is not None:  # the autotuner's choice for the timed stencil launches
         rt, sites, rb = tuned["shape"]
         out["stencil_shape"] = {"rhs_per_thread": rt, "sites_per_block": sites, "rhs_tiles_per_block": rb,
                                 "candidates_ms": {f"{a}x{b}x{c}": round(t, 4) for (a, b, c), t in tuned["ms"].items()}}
     g.destroy()
+    return out
+
+
+def run_variants(ovs, g, x, y, k, stream, w, steps=2):
+    """The method's variants on the timed workload's handle and batch (same
+    lattice, k, right-hand sides, mixed form): the harmonic variant (Sec. 4),
+    D_ov(mu) x (Sec. 2, Eq. Dov) and Schur deflation (Sec. 5.2) built from the
+    installed right vectors. Each: applications/s over `steps` CUDA-event
+    timed calls after one untimed call, the per-class device times of one
+    traced call, and the relative difference of the result from the LR form
+    at the same k (harmonic, Schur: a different approximation, not an
+    error)."""
+    import torch
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ovs.profile_enable(g, timing=True)
+        fn()
+        prof = ovs.profile_read(g)
+        ovs.profile_enable(g, timing=False)
+        per = {c: {"ms": round(v["ms"], 2), "gbs": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None}
+               for c, v in prof.items() if v["launches"]}
+        return {"value": round(w["nrhs"] / (ms / 1e3), 4), "unit": "applications/s", "ms_per_call": round(ms, 2),
+                "per_class": per}
+
+    def reldiff(a):
+        return float(torch.max(torch.linalg.vector_norm(a - y_lr, dim=1) / torch.linalg.vector_norm(y_lr, dim=1)))
+
+    out = {}
+    y_lr = torch.empty_like(x)
+    ovs.sign_apply(g, x, y_lr, k, prec=ovs.MIXED, stream=stream, want_info=False)
+    yv = torch.empty_like(x)
+    out["harmonic"] = timed(lambda: ovs.sign_apply(g, x, yv, k, prec=ovs.MIXED, stream=stream, want_info=False,
+                                                   harmonic=True))
+    out["harmonic"]["max_rel_diff_vs_lr"] = reldiff(yv)
+    out["overlap_apply"] = timed(lambda: ovs.overlap_apply(g, x, yv, k, prec=ovs.MIXED, stream=stream,
+                                                          want_info=False))
+    if w["m"] > 0:
+        R, _, _ = ovs.deflate_get(g)
+        ovs.deflate_load_schur(g, R)
+        del R
+        out["schur"] = timed(lambda: ovs.sign_apply(g, x, yv, k, prec=ovs.MIXED, stream=stream, want_info=False))
+        out["schur"]["max_rel_diff_vs_lr"] = reldiff(yv)
+        out["schur"]["basis"] = "Schur vectors of the LR set-up's right vectors (same m)"
     return out
 
 
@@ -520,6 +592,53 @@ def run_batched(args, world, rank, local, steps, warmup):
     return out
 
 
+def run_overlap_solve(args, world, rank, local):
+    """Nested inversion D_ov(mu) x = b (Sec. 2, Eq. Dov; Secs. 6, 7) on the
+    deflated FP64 configuration's lattice: 8^4, eps 0.7, seed 3, mu 0.2,
+    m_w -1.5, m = 30 critical vectors from the device set-up (tol 1e-9),
+    16 right-hand sides, inner k = 200, outer GMRES(20). Mixed inner form to
+    an outer tolerance of 1e-6, FP64 inner form to 1e-10. Reports the solve
+    time, the outer iterations (each one D_ov application of all right-hand
+    sides) and the true relative residuals."""
+    import numpy as np
+    import torch
+
+    import paper_0704_3486_gb300 as ovs
+    import synth
+
+    if not os.path.exists(ovs.LIB_PATH):
+        from paper_0704_3486_gb300 import build
+        build.build()
+    ovs.load()
+    torch.cuda.set_device(local)
+    dims, seed, eps, mu, m, k, nrhs, restart = (8, 8, 8, 8), 3, 0.7, 0.2, 30, 200, 16, 20
+    g = ovs.create_gauge(dims, seed, eps, ovs.MIXED)
+    ovs.set_mu(g, mu, -1.5)
+    t0 = time.perf_counter()
+    _, st_setup = ovs.deflate_setup(g, m, 1e-9, allow_unconverged=True)
+    t_setup = time.perf_counter() - t0
+    n = 12 * int(np.prod(dims))
+    b = torch.from_numpy(synth.gaussian_vectors(n, nrhs, 17)).cuda()
+    x = torch.empty_like(b)
+    out = {"metric": "D_ov(mu) x = b solves/s (nested GMRES around the deflated sign)", "unit": "solves/s",
+           "n_gpus": world, "data": "synthetic",
+           "config": {"workload": f"8^4 eps=0.7 mu=0.2 m={m} (device set-up {ovs.STATUS.get(st_setup)}, "
+                                  f"{t_setup:.1f} s), inner k={k}, GMRES({restart}), {nrhs} RHS",
+                      "lattice": list(dims), "m_deflated": m, "k": k, "restart": restart, "nrhs": nrhs}}
+    for name, prec, tol in (("mixed_inner", ovs.MIXED, 1e-6), ("fp64_inner", ovs.F64, 1e-10)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = ovs.overlap_solve(g, b, x, k, restart, tol, max_cycles=50, prec=prec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": round(dt, 3), "value": round(nrhs / dt, 4), "status": ovs.STATUS.get(st, st),
+                     "outer_iterations": info[0]["iters"], "cycles": info[0]["cycles"],
+                     "max_rel_resid": max(i["rel_resid"] for i in info), "tol": tol,
+                     "dov_applications_per_s": round(nrhs * (info[0]["iters"] + info[0]["cycles"]) / dt, 2)}
+    g.destroy()
+    return out
+
+
 def run_reference_full(w):
     """One complete oracle application (no sampling, no model): one
     right-hand side, LR deflation with m seeded random vectors, CGS2 Arnoldi
@@ -576,6 +695,11 @@ def main():
     if args.impl == "reference":
         out = run_reference_full(w) if args.full_application and rank == 0 else run_reference(args, w, world, rank)
         if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload == "overlap-solve":
+        out = run_overlap_solve(args, world, rank, local)
+        if rank == 0:
             print(json.dumps(out), flush=True)
         return
     if args.workload == "batched":

@@ -251,3 +251,33 @@ def test_mixed_batch_vs_fp64_single(gpu, name, m, k, budget):
         assert st == 0
         assert rel(y[r], y64.cpu().numpy()[0]) < 1e-6, (name, r)
     g.destroy()
+
+
+def test_free_field_sign_headline_size(gpu):
+    """The whole sign application at the timed workload's size and launch
+    configuration (16^3 x 32, mu = 0.1, k = 250, 16 right-hand sides in the
+    mixed form) on the free field, whose sgn(H_w) x the oracle gives exactly
+    for any x by the FFT closed form: every right-hand side, every entry.
+    The free spectrum is gapped (|lambda| >= ~0.2), so the Krylov truncation
+    at k = 250 is small (2e-10 on 8^3 x 16 with the oracle's own Arnoldi,
+    1.2e-9 here): tolerances 1e-6 (mixed) and 1e-8 (FP64, 4 right-hand
+    sides, the truncation plus margin)."""
+    dims, mu, k = (16, 16, 16, 32), 0.1, 250
+    v = int(np.prod(dims))
+    g = gpu.create_gauge_from_links(dims, synth.unit_links(dims), gpu.MIXED)
+    gpu.set_mu(g, mu, MW)
+    x = synth.gaussian_vectors(12 * v, 16, 79)
+    ref = [freefield.apply_free(x[r], dims, mu, MW, "sgnH") for r in range(16)]
+    xd = torch.from_numpy(x).to(DEV)
+    yd = torch.empty_like(xd)
+    st, info = gpu.sign_apply(g, xd, yd, k, prec=gpu.MIXED)
+    assert st == 0
+    y = yd.cpu().numpy()
+    errs = [rel(y[r], ref[r]) for r in range(16)]
+    assert max(errs) < 1e-6, errs
+    st, info = gpu.sign_apply(g, xd[:4].contiguous(), yd[:4], k, prec=gpu.F64)
+    assert st == 0
+    y = yd[:4].cpu().numpy()
+    errs = [rel(y[r], ref[r]) for r in range(4)]
+    assert max(errs) < 1e-8, errs
+    g.destroy()

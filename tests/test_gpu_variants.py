@@ -14,6 +14,7 @@ Tolerances (relative 2-norm per right-hand side):
 
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
 import torch
 
 import synth
@@ -278,25 +279,25 @@ def test_schur_matches_oracle_8to4(gpu):
 
 
 def test_schur_device_setup(gpu):
-    """ovs_deflate_setup_schur (right vectors only) at 6^4, m = 12: every
-    eigenvalue on the diagonal of the installed T_m is an eigenvalue of the
-    sparse oracle operator among its critical ones, and the application
+    """ovs_deflate_setup_schur (right vectors only) at 6^4, m = 12, tol 1e-8: every
+    eigenvalue on the diagonal of the installed T_m is one of the 2m
+    eigenvalues of the sparse operator nearest 0 (ARPACK shift-invert), and
+    the application
     with the installed S_m matches the oracle run on the same S_m."""
     dims, mu = (6, 6, 6, 6), 0.2
     v = int(np.prod(dims))
     links = synth.gauge_links(dims, 3, 0.6)
     h = lattice.hw_operator(links, dims, mu, MW)
-    hm = lattice.hw_operator(links, dims, -mu, MW)
     g = gpu.create_gauge_from_links(dims, links, gpu.MIXED)
     gpu.set_mu(g, mu, MW)
     m = 12
-    eig, st = gpu.deflate_setup(g, m, 1e-10, scheme="schur")
+    eig, st = gpu.deflate_setup(g, m, 1e-8, scheme="schur")
     assert st == 0 and gpu.deflate_scheme(g) == "schur"
-    lam_ref, _, _ = deflation.critical_pairs_sparse(h, hm, 3 * m, extra=m)
-    assert np.abs(eig[:, None] - lam_ref[None, :]).min(axis=1).max() < 1e-8
+    lam_ref = spla.eigs(h.tocsc(), k=2 * m, sigma=0.0, which="LM", tol=1e-12, return_eigenvectors=False)
+    assert np.abs(eig[:, None] - lam_ref[None, :]).min(axis=1).max() < 1e-6
     Sg, _, _ = gpu.deflate_get(g)
     S, T = schur.schur_from_eigvecs(lambda q: h @ q, Sg.T)
-    assert np.abs(np.tril(S.conj().T @ (h @ S), -1)).max() < 1e-8  # a partial Schur form
+    assert np.abs(np.tril(S.conj().T @ (h @ S), -1)).max() < 1e-6  # a partial Schur form
     x = synth.gaussian_vectors(12 * v, 2, 55)
     yd = torch.empty((2, 12 * v), dtype=torch.complex128, device=DEV)
     gpu.sign_apply(g, to_dev(x), yd, 80, prec=gpu.F64)
