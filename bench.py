@@ -429,8 +429,12 @@ def run_ours(args, w, world, rank, local):
                                   "share": share[c]} for c in prof}}
     launches = sum(p["launches"] for p in prof_count.values())
 
+    # the metric holds only at 1e-6: a batch whose mixed result misses the
+    # FP64 result at equal (m, k) by more on any right-hand side scores 0
+    metric_met = rel_err <= 1e-6
     out = {
-        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": round(value, 4) if metric_met else 0.0, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_of(w, world),
@@ -440,6 +444,12 @@ def run_ours(args, w, world, rank, local):
                             "within_1e-6": rel_err <= 1e-6,
                             "speedup_mixed_batched": round(value / world / fp64_value, 3)},
         "long_reference": long_ref,
+        "accuracy": {"metric_met": metric_met,
+                     "reading": "1e-6 = relative 2-norm of the mixed result against the FP64 result at equal "
+                                "(m, k), every right-hand side of the batch (max in fp64_single_rhs)",
+                     "deflation_basis": f"device set-up within its budget: status {setup['status']} "
+                                        f"(residuals in deflation_setup)",
+                     "krylov_truncation": "long_reference: FP64 at k against FP64 at k_long on the same basis"},
         "tracing": {"value_with_per_launch_events": round(traced_value, 4),
                     "overhead_frac": round(1.0 - traced_value / value, 4)},
         "deflation_setup": setup,

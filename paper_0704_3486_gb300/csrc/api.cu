@@ -878,36 +878,42 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
                              nullptr, nullptr, st));
         return OVS_OK;
     };
-    // partial sums of S^H v_r (reduced by the caller)
-    auto schur_dots = [&](const void* v) -> int {
-        KL(OVS_PROF_PROJ, bytes_dots(N, tp, m, nrhs, true),
-           launch_gdots(tp, 1, Sb, 0, units, m, v, units, nullptr, 0, false, units, plan, nrhs, kw.partial, kw.active,
-                        st));
+    // partial sums of S^H v_r over pblk blocks (reduced by the caller): in the
+    // mixed form the shared-basis kernel that reads S once for all
+    // right-hand sides, else the register sweep
+    const int sdb = (tp == PREC_F32 && m > 0) ? shared_dots_blocks(m, nrhs, units, g->num_sms, kw.nblk) : 0;
+    const int pblk = sdb > 0 ? sdb : plan.nblk;
+    auto shared_dots = [&](const void* basis, const void* v, const int* act) -> int {
+        if (sdb > 0)
+            KL(OVS_PROF_PROJ, bytes_dots(N, tp, m, nrhs, true),
+               launch_shared_dots(basis, units, m, v, units, nrhs, units, sdb, kw.partial, S1, act, st));
+        else
+            KL(OVS_PROF_PROJ, bytes_dots(N, tp, m, nrhs, true),
+               launch_gdots(tp, 1, basis, 0, units, m, v, units, nullptr, 0, false, units, plan, nrhs, kw.partial, act,
+                            st));
         return OVS_OK;
     };
+    auto schur_dots = [&](const void* v) -> int { return shared_dots(Sb, v, kw.active); };
     if (schur) {
         // c = S^H x, x_perp = x - S c, classical Gram-Schmidt applied twice
         CK(cudaMemsetAsync(kw.active, 0xff, sizeof(int) * nrhs, st));
         TRY(schur_dots(w.xint));
-        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
-           launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef, m, false, nullptr, st));
+        KL(OVS_PROF_SMALL, 16.0 * pblk * S1 * nrhs,
+           launch_reduce(kw.partial, pblk, S1, m, nrhs, kw.cdef, m, false, nullptr, st));
         TRY(schur_out(kw.cdef, m, w.xint));
         TRY(schur_dots(w.xint));
-        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
-           launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef2, m, false, nullptr, st));
+        KL(OVS_PROF_SMALL, 16.0 * pblk * S1 * nrhs,
+           launch_reduce(kw.partial, pblk, S1, m, nrhs, kw.cdef2, m, false, nullptr, st));
         TRY(schur_out(kw.cdef2, m, w.xint));
-        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
-           launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef, m, true, nullptr, st));
+        KL(OVS_PROF_SMALL, 16.0 * pblk * S1 * nrhs,
+           launch_reduce(kw.partial, pblk, S1, m, nrhs, kw.cdef, m, true, nullptr, st));
         CK(cudaMemsetAsync(w.yacc, 0, f64 * nrhs, st));
     } else if (m > 0) {
         const void* Lb = tp == PREC_F64 ? g->L64 : g->L32;
         const void* Rb = tp == PREC_F64 ? g->R64 : g->R32;
-        const int S = gdots_stride(1, m);
-        KL(OVS_PROF_PROJ, bytes_dots(N, tp, m, nrhs, true),
-           launch_gdots(tp, 1, Lb, 0, units, m, w.xint, units, nullptr, 0, false, units, plan, nrhs, kw.partial,
-                        nullptr, st));
-        KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S * nrhs,
-           launch_reduce(kw.partial, plan.nblk, S, m, nrhs, kw.cdef, m, false, nullptr, st));
+        TRY(shared_dots(Lb, w.xint, nullptr));
+        KL(OVS_PROF_SMALL, 16.0 * pblk * S1 * nrhs,
+           launch_reduce(kw.partial, pblk, S1, m, nrhs, kw.cdef, m, false, nullptr, st));
         KL(OVS_PROF_SMALL, 32.0 * m * nrhs, launch_sign_scale(kw.cdef, g->sgn, m, nrhs, kw.cdef2, st));
         if (tp == PREC_F32 && m <= 1536)
             KL(OVS_PROF_PROJ, bytes_update(N, tp, tp, m, nrhs, true, true),
@@ -956,15 +962,15 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
             // xz = S^H z (both passes) lands in column j of X
             char* Xj = (char*)kw.X + sizeof(double2) * (size_t)j * m;
             TRY(schur_dots(w.wvec));
-            KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
-               launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, Xj, x_rhs, false, kw.active, st));
+            KL(OVS_PROF_SMALL, 16.0 * pblk * S1 * nrhs,
+               launch_reduce(kw.partial, pblk, S1, m, nrhs, Xj, x_rhs, false, kw.active, st));
             TRY(schur_out(Xj, x_rhs, w.wvec));
             TRY(schur_dots(w.wvec));
-            KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
-               launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, kw.cdef2, m, false, kw.active, st));
+            KL(OVS_PROF_SMALL, 16.0 * pblk * S1 * nrhs,
+               launch_reduce(kw.partial, pblk, S1, m, nrhs, kw.cdef2, m, false, kw.active, st));
             TRY(schur_out(kw.cdef2, m, w.wvec));
-            KL(OVS_PROF_SMALL, 16.0 * plan.nblk * S1 * nrhs,
-               launch_reduce(kw.partial, plan.nblk, S1, m, nrhs, Xj, x_rhs, true, kw.active, st));
+            KL(OVS_PROF_SMALL, 16.0 * pblk * S1 * nrhs,
+               launch_reduce(kw.partial, pblk, S1, m, nrhs, Xj, x_rhs, true, kw.active, st));
         }
         const bool tma = (tp == PREC_F32) && tma_update_fits(j);
         const bool chunked = (tp == PREC_F32) && gdots_chunk_fits(j);

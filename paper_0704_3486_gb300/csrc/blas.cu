@@ -600,6 +600,133 @@ __global__ void k_sign_scale(const double2* __restrict__ c, const double* __rest
     out[idx] = make_double2(sgn[i] * v.x, sgn[i] * v.y);
 }
 
+// ------------------------------------------------------- shared-basis dots
+// Inner products against a complex64 basis shared by all right-hand sides
+// (the LR projection L^+ x, the Schur projections S^H z of every Arnoldi
+// step): partial[(r*nblk + b)*pstride + i] = sum over the units of chunk b
+// of S_i^H z_r, i < m, r < nrhs. A block takes one chunk of units and stages
+// it KD units at a time, every S_i and every z_r, in shared memory (unit-
+// major, so that the threads of a warp read consecutive vectors); each
+// thread accumulates a tile of 4 basis vectors x 2 right-hand sides: FP32
+// over one staged tile (2 KD complex terms), FP64 across tiles. Each
+// element of the basis is read from memory once per call, not once per
+// right-hand side.
+constexpr int KD = 32;
+
+__global__ void __launch_bounds__(BT) k_shared_dots(const float4* __restrict__ S, long long svec, int m,
+                                                    const float4* __restrict__ Z, long long zstride, int nrhs,
+                                                    long long nunits, long long chunk, int nblk,
+                                                    double2* __restrict__ partial, int pstride,
+                                                    const int* __restrict__ active) {
+    extern __shared__ float4 sd_smem[];
+    float4* sS = sd_smem;                   // [KD][m]
+    float4* sZ = sd_smem + (size_t)KD * m;  // [KD][nrhs]
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const long long u0 = (long long)b * chunk;
+    const long long u1 = min(u0 + chunk, nunits);
+    const int itiles = (m + 3) / 4, rtiles = (nrhs + 1) / 2;
+    const int ti = tid % itiles, tr = tid / itiles;
+    const bool work = tr < rtiles;
+    double acc[4][2][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) acc[a][c][0] = acc[a][c][1] = 0.0;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long t0 = u0; t0 < u1; t0 += KD) {
+        const int cnt = (int)min((long long)KD, u1 - t0);
+        for (int idx = tid; idx < m * KD; idx += BT) {
+            const int i = idx / KD, u = idx - i * KD;
+            sS[(size_t)u * m + i] = (u < cnt) ? __ldg(S + (size_t)i * svec + t0 + u) : zero;
+        }
+        for (int idx = tid; idx < nrhs * KD; idx += BT) {
+            const int r = idx / KD, u = idx - r * KD;
+            sZ[(size_t)u * nrhs + r] = (u < cnt) ? __ldg(Z + (size_t)r * zstride + t0 + u) : zero;
+        }
+        __syncthreads();
+        if (work) {
+            float a32[4][2][2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) a32[a][c][0] = a32[a][c][1] = 0.f;
+            for (int u = 0; u < cnt; ++u) {
+                float4 sv[4], zv[2];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = ti + q * itiles;
+                    sv[q] = (i < m) ? sS[(size_t)u * m + i] : zero;
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int r = tr + q * rtiles;
+                    zv[q] = (r < nrhs) ? sZ[(size_t)u * nrhs + r] : zero;
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {  // conj(s) z for the two complex numbers of the unit
+                        float re = a32[a][c][0], im = a32[a][c][1];
+                        re = fmaf(sv[a].x, zv[c].x, re);
+                        re = fmaf(sv[a].y, zv[c].y, re);
+                        re = fmaf(sv[a].z, zv[c].z, re);
+                        re = fmaf(sv[a].w, zv[c].w, re);
+                        im = fmaf(sv[a].x, zv[c].y, im);
+                        im = fmaf(-sv[a].y, zv[c].x, im);
+                        im = fmaf(sv[a].z, zv[c].w, im);
+                        im = fmaf(-sv[a].w, zv[c].z, im);
+                        a32[a][c][0] = re;
+                        a32[a][c][1] = im;
+                    }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    acc[a][c][0] += (double)a32[a][c][0];
+                    acc[a][c][1] += (double)a32[a][c][1];
+                }
+        }
+        __syncthreads();
+    }
+    if (!work) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int i = ti + a * itiles, r = tr + c * rtiles;
+            if (i >= m || r >= nrhs) continue;
+            if (active != nullptr && active[r] == 0) continue;
+            partial[((size_t)r * nblk + b) * pstride + i] = make_double2(acc[a][c][0], acc[a][c][1]);
+        }
+}
+
+// Blocks of the shared-basis dots for nunits within the partial slots
+// available; 0 when the tile does not fit (the register sweep k_gdots
+// serves then).
+int shared_dots_blocks(int m, int nrhs, long long nunits, int num_sms, int max_blocks) {
+    const int itiles = (m + 3) / 4, rtiles = (nrhs + 1) / 2;
+    if (m < 1 || nrhs < 1 || (long long)itiles * rtiles > BT) return 0;
+    if ((size_t)(m + nrhs) * KD * sizeof(float4) > 200 * 1024) return 0;
+    long long want = 2LL * num_sms;
+    want = std::min<long long>(want, std::max<long long>(1, nunits / KD));
+    want = std::min<long long>(want, max_blocks);
+    return want < 1 ? 0 : (int)want;
+}
+
+cudaError_t launch_shared_dots(const void* S, long long svec, int m, const void* Z, long long zstride, int nrhs,
+                               long long nunits, int nblk, void* partial, int pstride, const int* active,
+                               cudaStream_t st) {
+    const size_t smem = (size_t)(m + nrhs) * KD * sizeof(float4);
+    cudaError_t e = ensure_dyn_smem((const void*)k_shared_dots, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    long long chunk = (nunits + nblk - 1) / nblk;
+    chunk = ((chunk + KD - 1) / KD) * KD;
+    k_shared_dots<<<nblk, BT, smem, st>>>((const float4*)S, svec, m, (const float4*)Z, zstride, nrhs, nunits, chunk,
+                                         nblk, (double2*)partial, pstride, active);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launch
 BlasPlan blas_plan(long long nunits, int nrhs, int num_sms) {
     BlasPlan p;

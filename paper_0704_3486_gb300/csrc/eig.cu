@@ -695,7 +695,14 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
     c.g = g;
     c.st = 0;
     c.N = g->N;
-    c.p = (int)std::min<long long>(m + std::max(8, (m + 1) / 2), g->N / 2);
+    // block size p > m: the cut of the filter sits at the p-th Ritz value.
+    // OVS_SETUP_BLOCK=<p> in the environment overrides it (a diagnosis aid).
+    long long pb = m + std::max(8, (m + 1) / 2);
+    if (const char* ev = std::getenv("OVS_SETUP_BLOCK")) {
+        const long long v = std::atoll(ev);
+        if (v > m) pb = v;
+    }
+    c.p = (int)std::min<long long>(pb, g->N / 2);
     if (c.p > 65535) return lib_fail(OVS_EINVAL, "m too large for the set-up block");
     const int p = c.p;
     const long long N = c.N;

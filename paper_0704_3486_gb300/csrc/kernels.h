@@ -89,6 +89,13 @@ cudaError_t launch_update(int prec_v, int prec_out, const void* basis, long long
 cudaError_t launch_shared_combine(int prec_out, const void* R, long long vec_stride, int m, const void* coef,
                                   long long coef_stride, double alpha, const void* in, long long in_rhs_stride,
                                   void* out, long long out_rhs_stride, long long nunits, int nrhs, cudaStream_t st);
+// inner products against a complex64 basis S shared by all right-hand sides,
+// read once per call: partial[r][b][i] (row stride pstride) for the nblk
+// chunks b, i < m; nblk from shared_dots_blocks (0: not applicable)
+int shared_dots_blocks(int m, int nrhs, long long nunits, int num_sms, int max_blocks);
+cudaError_t launch_shared_dots(const void* S, long long svec, int m, const void* Z, long long zstride, int nrhs,
+                               long long nunits, int nblk, void* partial, int pstride, const int* active,
+                               cudaStream_t st);
 // sum partial[r][b][i] (row stride pstride) over b -> out[r*out_stride + i], i < J
 cudaError_t launch_reduce(const void* partial, int nblk, int pstride, int J, int nrhs, void* out,
                           long long out_stride, bool accumulate, const int* active, cudaStream_t st);
