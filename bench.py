@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 METRIC = "sgn(H_w(μ))x applications/s at 1e-6 rel err, mixed+batched vs plain FP64"
 UNIT = "applications/s"
 DEFAULT = dict(dims=(16, 16, 16, 32), eps=0.6, seed=5, mu=0.1, m_w=-1.5, m=100, k=250, nrhs=16, src_seed=2,
-               eig_tol=1e-6, setup_budget_s=90.0)
+               eig_tol=1e-6, setup_budget_s=150.0)
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")

@@ -1047,7 +1047,7 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
         // Schur coefficients sgn(T) c + beta Y e_1 (App. A), then y = S cS
         KL(OVS_PROF_SMALL, 16.0 * ((double)m * k * 4 + (double)k * k) * nrhs,
            launch_schur_coeff(g->schurT, g->schurFT, m, kw.X, x_rhs, kw.H, h_rhs, ldh, kw.newton, 2 * kmax * kmax,
-                              kw.k_used, kw.status, kw.beta, kw.cdef, m, kw.sylv, kw.cS, m, nrhs, st));
+                              kw.k_used, kw.status, kw.beta, kw.cdef, m, kw.sylv, kw.cS, m, nrhs, k, st));
         if (tp == PREC_F64)
             KL(OVS_PROF_PROJ, bytes_update(N, PREC_F64, PREC_F64, m, nrhs, true, false),
                launch_update(PREC_F64, PREC_F64, g->R64, 0, N, m, nullptr, kw.cS, m, 1.0, nullptr, 0, w.yacc, N, N,

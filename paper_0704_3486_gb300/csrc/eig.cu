@@ -92,6 +92,57 @@ __global__ void k_ritz_resid32(const float2* __restrict__ Z, const float2* __res
     }
 }
 
+// Per column i of Q (complex128): Rayleigh quotient theta_i = q^H w / q^H q
+// and residual ||w - theta_i q|| / ||q|| with W = H Q (one block per column).
+__global__ void k_rq_resid(const double2* __restrict__ W, const double2* __restrict__ Q, long long N,
+                           double2* __restrict__ theta, double* __restrict__ out) {
+    __shared__ double sh[4][32];
+    __shared__ double2 s_t;
+    const int i = blockIdx.x;
+    const double2* w = W + (size_t)i * N;
+    const double2* q = Q + (size_t)i * N;
+    double ar = 0.0, ai = 0.0, qq = 0.0;
+    for (long long n = threadIdx.x; n < N; n += blockDim.x) {
+        const double2 a = q[n], b = w[n];
+        ar += a.x * b.x + a.y * b.y;
+        ai += a.x * b.y - a.y * b.x;
+        qq += a.x * a.x + a.y * a.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        qq += __shfl_xor_sync(0xffffffffu, qq, o);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][wp] = ar; sh[1][wp] = ai; sh[2][wp] = qq; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, ti = 0.0, tq = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { tr += sh[0][k]; ti += sh[1][k]; tq += sh[2][k]; }
+        s_t = tq > 0.0 ? make_double2(tr / tq, ti / tq) : make_double2(0.0, 0.0);
+        sh[3][0] = tq;
+        theta[i] = s_t;
+    }
+    __syncthreads();
+    const double2 t = s_t;
+    double s = 0.0;
+    for (long long n = threadIdx.x; n < N; n += blockDim.x) {
+        const double2 a = q[n], b = w[n];
+        const double rx = b.x - (t.x * a.x - t.y * a.y);
+        const double ry = b.y - (t.x * a.y + t.y * a.x);
+        s += rx * rx + ry * ry;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) sh[0][wp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += sh[0][k];
+        out[i] = sh[3][0] > 0.0 ? sqrt(tot / sh[3][0]) : 0.0;
+    }
+}
+
 // U[:, j] *= 1/sqrt(max(lam_j, floor)) (column-major p x p)
 __global__ void k_scale_cols(double2* __restrict__ U, const double* __restrict__ lam, int p, double floor_) {
     const int j = blockIdx.x;
@@ -355,6 +406,25 @@ int rayleigh_ritz32(Ctx& c, double mu, void* Q, void* Z, void* X, void* ZX,
     return OVS_OK;
 }
 
+// Complex128 residuals of the Ritz pairs in Q (complex128, the vectors of a
+// complex64 Rayleigh-Ritz): W = H Q in complex128, then per vector its
+// Rayleigh quotient and residual (k_rq_resid). No block algebra: each pair
+// is certified on its own, at the cost of one complex128 stencil.
+int pair_residuals64(Ctx& c, double mu, std::vector<std::complex<double>>& theta, std::vector<double>& resid) {
+    const int p = c.p;
+    const long long N = c.N;
+    int rc = apply_h(c, PREC_F64, c.Q, c.W, mu);
+    if (rc) return rc;
+    k_rq_resid<<<p, 256, 0, c.st>>>(c.W, c.Q, N, c.theta, c.resid);
+    ECK(cudaGetLastError());
+    theta.resize(p);
+    resid.resize(p);
+    ECK(cudaMemcpyAsync(theta.data(), c.theta, sizeof(double2) * p, cudaMemcpyDeviceToHost, c.st));
+    ECK(cudaMemcpyAsync(resid.data(), c.resid, sizeof(double) * p, cudaMemcpyDeviceToHost, c.st));
+    ECK(cudaStreamSynchronize(c.st));
+    return OVS_OK;
+}
+
 struct SideResult {
     std::vector<std::complex<double>> theta;
     std::vector<double> resid;
@@ -485,6 +555,7 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
     double last_iter_s = 0.0;
     bool have64 = false;  // the last pairs come from a complex128 Rayleigh-Ritz (Q holds them)
     bool switched = false;  // this iteration left complex64
+    int last_nconv = 0;     // most wanted pairs at tol so far (complex64 residuals)
     if (c64) ECK(launch_convert(PREC_F32, c.Q, c.F[0], (long long)p * N, c.st));
     auto sort_order = [&]() {
         std::iota(order.begin(), order.end(), 0);
@@ -495,6 +566,23 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
         double r = 0.0;
         for (int i = 0; i < m; ++i) r = std::max(r, res.resid[order[i]] / hnorm);
         return r;
+    };
+    // convergence measure: the m-th smallest residual over the whole block,
+    // i.e. m pairs at tol. The pairs installed are the m of smallest
+    // |Re theta| among those at tol. Ritz values of unresolved directions
+    // (residuals stuck at ~1e-2 while their |theta| wanders from one
+    // iteration to the next) may sit among the smallest |theta|; they are
+    // not eigenvalues and are not installed.
+    auto mth_resid = [&]() {
+        std::vector<double> rr(p);
+        for (int i = 0; i < p; ++i) rr[i] = res.resid[i] / hnorm;
+        std::nth_element(rr.begin(), rr.begin() + (m - 1), rr.end());
+        return rr[m - 1];
+    };
+    auto count_at_tol = [&]() {
+        int n = 0;
+        for (int i = 0; i < p; ++i) n += res.resid[i] / hnorm <= tol;
+        return n;
     };
     // progress measure: the median residual of the m wanted pairs (the
     // largest one, at the edge of the wanted set, converges slowest)
@@ -520,6 +608,16 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
     };
     // complex128 Rayleigh-Ritz of the block in Q (orthonormalised first);
     // Q then holds the Ritz vectors
+    // complex128 residuals of the complex64 Ritz pairs now in Q, pair by pair
+    auto certify_pairs = [&](int it) -> int {
+        int r2 = pair_residuals64(c, mu, res.theta, res.resid);
+        if (r2) return r2;
+        res.matvecs += p;
+        sort_order();
+        have64 = true;
+        report(it, "c128 residuals", max_resid());
+        return OVS_OK;
+    };
     auto certify = [&](int it) -> int {
         int r2 = svqb(c);
         if (r2) return r2;
@@ -560,24 +658,38 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
             ECK(cudaMemcpyAsync(c.F[0], c.A1, sizeof(float2) * p * N, cudaMemcpyDeviceToDevice, c.st));
             have64 = false;
             sort_order();
-            const double r32 = max_resid();
-            report(it, "c64", r32);
+            report(it, "c64", max_resid());
+            const double r32 = mth_resid();
+            // progress: more pairs at tol, or a falling median
             const double med = median_resid();
-            const bool stalled = it > 0 && med > 0.7 * last_rmax32;
-            last_rmax32 = med;
+            const int nconv = count_at_tol();
+            const bool stalled = it > 0 && med > 0.7 * last_rmax32 && nconv <= last_nconv;
+            last_rmax32 = std::min(last_rmax32, med);
+            last_nconv = std::max(last_nconv, nconv);
             rmax = r32;
             if (r32 <= tol || stalled) {
-                // certify in complex128
+                // certify in complex128, pair by pair (one complex128 stencil)
                 ECK(launch_convert(PREC_F64, c.F[0], c.Q, (long long)p * N, c.st));
-                rc = certify(it);
+                rc = certify_pairs(it);
                 if (rc) return rc;
-                rmax = max_resid();
-                if (rmax > tol && stalled) {
-                    c64 = false;  // complex64 has reached its limit: complex128 filtering from here,
-                    switched = true;  // whose stencil is FP64-ALU bound and ~20x slower per degree
-                } else if (rmax > tol) {
-                    ECK(launch_convert(PREC_F32, c.Q, c.F[0], (long long)p * N, c.st));
+                rmax = mth_resid();
+                if (rmax > tol && (rmax < 100.0 * tol || rmax < 1e-5)) {
+                    // close to tol: a complex128 Rayleigh-Ritz on the block
+                    rc = certify(it);
+                    if (rc) return rc;
+                    rmax = mth_resid();
+                    if (rmax > tol && stalled) {
+                        // complex64 rounding is what keeps the pairs from
+                        // tol: complex128 filtering from here, whose stencil
+                        // is FP64-ALU bound and ~20x slower per degree
+                        c64 = false;
+                        switched = true;
+                    } else if (rmax > tol) {
+                        ECK(launch_convert(PREC_F32, c.Q, c.F[0], (long long)p * N, c.st));
+                    }
                 }
+                // far from tol: the slow pairs need more filtering, not more
+                // precision; the complex64 block in F[0] carries on
             }
         } else {
             void* bufs[3] = {c.Q, c.A1, c.A2};
@@ -588,7 +700,7 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
             res.matvecs += 2LL * fp.deg * p;
             rc = certify(it);
             if (rc) return rc;
-            rmax = max_resid();
+            rmax = mth_resid();
         }
         res.iters = it + 1;
         if (rmax <= tol && have64) {
@@ -614,9 +726,9 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
     }
     if (!have64) {  // the last pairs are complex64 ones: certify them
         ECK(launch_convert(PREC_F64, c.F[0], c.Q, (long long)p * N, c.st));
-        rc = certify(res.iters);
+        rc = certify_pairs(res.iters);
         if (rc) return rc;
-        res.converged = max_resid() <= tol;
+        res.converged = mth_resid() <= tol;
     }
     // hand the Ritz vectors (now in Q) to the caller, sorted by |theta|
     std::vector<std::complex<double>> th(p);
@@ -697,7 +809,12 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
     c.N = g->N;
     // block size p > m: the cut of the filter sits at the p-th Ritz value.
     // OVS_SETUP_BLOCK=<p> in the environment overrides it (a diagnosis aid).
-    long long pb = m + std::max(8, (m + 1) / 2);
+    // For m >= 64 the block is 2.5 m: the wanted edge of such a set lies in
+    // a dense part of the spectrum, where a cut at 1.5 m sits only a few per
+    // cent above it (at 16^3 x 32, m = 100: |lambda| 0.0454 vs 0.0479) and
+    // the filter separates the two slowly; with the cut at 2.5 m (0.054)
+    // the median residual fell ~10x per iteration instead of ~4x.
+    long long pb = m < 64 ? m + std::max(8, (m + 1) / 2) : m + (3LL * m + 1) / 2;
     if (const char* ev = std::getenv("OVS_SETUP_BLOCK")) {
         const long long v = std::atoll(ev);
         if (v > m) pb = v;
@@ -749,37 +866,53 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
         cudaFree(Rblk);
         SETUP_FAIL(rc);
     }
-    // choose m converged right pairs of smallest |Re lambda|; match left ones
-    std::vector<int> cand;
-    for (int i = 0; i < p; ++i)
-        if (right.resid[i] <= tol) cand.push_back(i);
-    bool ok = right.converged && left.converged;
-    if ((int)cand.size() < m) {
-        cand.clear();
-        for (int i = 0; i < m; ++i) cand.push_back(i);
-        ok = false;
-    }
-    std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) {
+    // choose the m right pairs of smallest |Re lambda| that are at tol and
+    // have a left partner at tol (eigenvalue conj(lambda), relative distance
+    // <= 1e-6); if fewer than m qualify, fill up with the nearest pairs in
+    // the same order and report OVS_EEIG
+    std::vector<int> order_r(p);
+    std::iota(order_r.begin(), order_r.end(), 0);
+    std::stable_sort(order_r.begin(), order_r.end(), [&](int x, int y) {
+        const bool cx = right.resid[x] <= tol, cy = right.resid[y] <= tol;
+        if (cx != cy) return cx;  // pairs at tol first
         return std::fabs(right.theta[x].real()) < std::fabs(right.theta[y].real());
     });
-    cand.resize(m);
-    std::vector<int> lsel(m, -1);
+    std::vector<int> cand, lsel;
     std::vector<char> used(p, 0);
     double worst_match = 0.0;
-    for (int i = 0; i < m; ++i) {
-        const std::complex<double> want = std::conj(right.theta[cand[i]]);
+    auto nearest_left = [&](int ri, bool at_tol, double* dist) {
+        const std::complex<double> want = std::conj(right.theta[ri]);
         int best = -1;
         double bd = 1e300;
         for (int j = 0; j < p; ++j) {
-            if (used[j]) continue;
+            if (used[j] || (at_tol && !(left.resid[j] <= tol))) continue;
             const double d = std::abs(left.theta[j] - want);
             if (d < bd) { bd = d; best = j; }
         }
-        used[best] = 1;
-        lsel[i] = best;
-        worst_match = std::max(worst_match, bd / std::max(std::abs(want), 1e-300));
+        *dist = bd / std::max(std::abs(want), 1e-300);
+        return best;
+    };
+    for (int q = 0; q < p && (int)cand.size() < m; ++q) {  // both sides at tol, matched
+        const int ri = order_r[q];
+        if (!(right.resid[ri] <= tol)) break;
+        double d = 0.0;
+        const int lj = nearest_left(ri, true, &d);
+        if (lj < 0 || d > 1e-6) continue;
+        used[lj] = 1;
+        cand.push_back(ri);
+        lsel.push_back(lj);
     }
-    if (worst_match > 1e-6) ok = false;
+    bool ok = (int)cand.size() == m;
+    for (int q = 0; q < p && (int)cand.size() < m; ++q) {  // fill up
+        const int ri = order_r[q];
+        if (std::find(cand.begin(), cand.end(), ri) != cand.end()) continue;
+        double d = 0.0;
+        const int lj = nearest_left(ri, false, &d);
+        used[lj] = 1;
+        cand.push_back(ri);
+        lsel.push_back(lj);
+        worst_match = std::max(worst_match, d);
+    }
     // canonical copies of the chosen vectors, then install (biorthonormalises L)
     double2 *Rc = nullptr, *Lc = nullptr, *tmp = nullptr;
     const size_t fv = sizeof(double2) * (size_t)N;

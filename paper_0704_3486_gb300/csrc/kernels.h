@@ -172,7 +172,7 @@ long long schur_scratch_per_rhs(int m);
 cudaError_t launch_schur_coeff(const void* T, const void* fT, int m, const void* X, long long x_rhs, const void* H,
                                long long h_rhs, int ldh, const void* fH, long long fh_rhs, const int* k_used,
                                const int* status, const double* beta, const void* c, long long c_stride,
-                               void* scratch, void* cS, long long cs_stride, int nrhs, cudaStream_t st);
+                               void* scratch, void* cS, long long cs_stride, int nrhs, int kmax, cudaStream_t st);
 // ---- outer GMRES of the overlap solve (solve.cu); canonical complex128
 int norm_blocks();  // partials per right-hand side of the norm kernels
 // norm[r] = ||v_r||, inv[r] = 1/norm[r] (inv may be nullptr); partial: nrhs x norm_blocks()

@@ -117,25 +117,10 @@ __global__ void __launch_bounds__(256) k_schur_coeff(
     const cd* F = reinterpret_cast<const cd*>(fH) + r * fh_rhs;
     cd* C = reinterpret_cast<cd*>(scratch) + r * scr_rhs;
     cd* Y = C + (size_t)m * kSylvMaxK;
+    (void)Xr;
+    (void)F;
     if (krylov) {
-        // C = sgn(T) X - X sgn(H_k)
-        for (int idx = tid; idx < m * n; idx += nt) {
-            const int i = idx / n, j = idx - i * n;
-            double re = 0.0, im = 0.0;
-            for (int l = i; l < m; ++l) {  // sgn(T) is upper triangular
-                const double2 a = fT[i + (long long)l * m], b = Xr[l + (long long)j * m];
-                re += a.x * b.x - a.y * b.y;
-                im += a.x * b.y + a.y * b.x;
-            }
-            for (int l = 0; l < n; ++l) {
-                const double2 a = Xr[i + (long long)l * m];
-                const cd b = F[(size_t)l * n + j];
-                re -= a.x * b.re - a.y * b.im;
-                im -= a.x * b.im + a.y * b.re;
-            }
-            C[(size_t)i * n + j] = {re, im};
-        }
-        __syncthreads();
+        // C = sgn(T) X - X sgn(H_k) was formed by k_schur_cmat
         for (int i = m - 1; i >= 0; --i) {
             // c~_ij = c_ij - sum_{l > i} T_il y_lj
             for (int j = tid; j < n; j += nt) {
@@ -212,10 +197,71 @@ cudaError_t launch_schur_xcol(void* X, long long x_rhs, int m, int j, const void
 bool schur_coeff_fits(int kmax) { return kmax <= kSylvMaxK; }
 long long schur_scratch_per_rhs(int m) { return 2LL * m * kSylvMaxK; }
 
+// C = sgn(T) X - X sgn(H_k) for every right-hand side (row-major m x n,
+// n = k_used[r], at the start of its scratch): a tiled complex product, one
+// 16 x 16 tile of C per block, the factors staged in shared memory 16 terms
+// at a time. Grid (column tiles, row tiles, right-hand sides) over the
+// largest n; tiles beyond a right-hand side's n do nothing.
+constexpr int TC = 16;
+__global__ void __launch_bounds__(TC * TC) k_schur_cmat(const double2* __restrict__ fT, int m,
+                                                        const double2* __restrict__ X, long long x_rhs,
+                                                        const double2* __restrict__ fH, long long fh_rhs,
+                                                        const int* __restrict__ k_used,
+                                                        const int* __restrict__ status,
+                                                        double2* __restrict__ scratch, long long scr_rhs) {
+    __shared__ double2 As[TC][TC + 1], Bs[TC][TC + 1];
+    const int r = blockIdx.z;
+    const int n = k_used[r];
+    if (n <= 0 || status[r] < 0) return;  // uniform over the block
+    const int i0 = blockIdx.y * TC, j0 = blockIdx.x * TC;
+    if (i0 >= m || j0 >= n) return;       // uniform over the block
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = i0 + ty, j = j0 + tx;
+    const double2* Xr = X + r * x_rhs;
+    const double2* F = fH + r * fh_rhs;  // row-major n x n
+    double re = 0.0, im = 0.0;
+    // sgn(T) X: A[i][l] = fT[i + l m], B[l][j] = X[l + j m], l < m
+    for (int k0 = 0; k0 < m; k0 += TC) {
+        const int la = k0 + tx, lb = k0 + ty;
+        As[ty][tx] = (i < m && la < m) ? fT[i + (long long)la * m] : make_double2(0.0, 0.0);
+        Bs[ty][tx] = (lb < m && j < n) ? Xr[lb + (long long)j * m] : make_double2(0.0, 0.0);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TC; ++q) {
+            const double2 a = As[ty][q], b = Bs[q][tx];
+            re = fma(a.x, b.x, re);
+            re = fma(-a.y, b.y, re);
+            im = fma(a.x, b.y, im);
+            im = fma(a.y, b.x, im);
+        }
+        __syncthreads();
+    }
+    // - X sgn(H_k): A[i][l] = X[i + l m], B[l][j] = F[l n + j], l < n
+    for (int k0 = 0; k0 < n; k0 += TC) {
+        const int la = k0 + tx, lb = k0 + ty;
+        As[ty][tx] = (i < m && la < n) ? Xr[i + (long long)la * m] : make_double2(0.0, 0.0);
+        Bs[ty][tx] = (lb < n && j < n) ? F[(size_t)lb * n + j] : make_double2(0.0, 0.0);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TC; ++q) {
+            const double2 a = As[ty][q], b = Bs[q][tx];
+            re = fma(-a.x, b.x, re);
+            re = fma(a.y, b.y, re);
+            im = fma(-a.x, b.y, im);
+            im = fma(-a.y, b.x, im);
+        }
+        __syncthreads();
+    }
+    if (i < m && j < n) scratch[r * scr_rhs + (size_t)i * n + j] = make_double2(re, im);
+}
+
 cudaError_t launch_schur_coeff(const void* T, const void* fT, int m, const void* X, long long x_rhs, const void* H,
                                long long h_rhs, int ldh, const void* fH, long long fh_rhs, const int* k_used,
                                const int* status, const double* beta, const void* c, long long c_stride,
-                               void* scratch, void* cS, long long cs_stride, int nrhs, cudaStream_t st) {
+                               void* scratch, void* cS, long long cs_stride, int nrhs, int kmax, cudaStream_t st) {
+    const dim3 grid((kmax + TC - 1) / TC, (m + TC - 1) / TC, nrhs);
+    k_schur_cmat<<<grid, dim3(TC, TC), 0, st>>>((const double2*)fT, m, (const double2*)X, x_rhs, (const double2*)fH,
+                                                fh_rhs, k_used, status, (double2*)scratch, schur_scratch_per_rhs(m));
     k_schur_coeff<<<nrhs, 256, 0, st>>>((const double2*)T, (const double2*)fT, m, (const double2*)X, x_rhs,
                                         (const double2*)H, h_rhs, ldh, (const double2*)fH, fh_rhs, k_used, status,
                                         beta, (const double2*)c, c_stride, (double2*)scratch,
