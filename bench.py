@@ -57,6 +57,12 @@ def parse_args():
                    help="batched: the multi-instance recipe (32 instances of 4^4/6^4/8^4, m = 20 each, "
                         "per-vector convergence stop) in one ovs_sign_apply_batched call; its own JSON line")
     p.add_argument("--instances", type=int, default=32)
+    p.add_argument("--batched-tol", type=float, default=1e-8, help="per-vector stop of the batched workload")
+    p.add_argument("--batched-cap", type=int, default=600, help="Krylov cap of the batched workload")
+    p.add_argument("--batched-every", type=int, default=10, help="check interval of the batched workload")
+    p.add_argument("--batched-prec", choices=["mixed", "f64"], default="mixed")
+    p.add_argument("--batched-every-check", action="store_true",
+                   help="batched workload: check every interval instead of the skip-ahead schedule")
     p.add_argument("--full-application", action="store_true",
                    help="with --impl reference: time one complete oracle application instead of samples")
     p.add_argument("--no-variants", action="store_true",
@@ -526,8 +532,9 @@ def run_batched(args, world, rank, local, steps, warmup):
     """The batched multi-instance workload: synth.batched_instances recipe,
     device set-up of 20 deflation vectors per instance (1 s budget each),
     one ovs_sign_apply_batched of all instances with the per-vector stop
-    (check every 10 steps, tol 1e-6, cap k = 300), mixed form. Applications/s
-    counts every right-hand side of every instance per call."""
+    (by default tol 1e-8 within k = 600, checks on multiples of 10 steps on
+    the skip-ahead schedule), mixed form. Applications/s counts every
+    right-hand side of every instance per call."""
     import numpy as np
     import torch
 
@@ -540,7 +547,9 @@ def run_batched(args, world, rank, local, steps, warmup):
     ovs.load()
     torch.cuda.set_device(local)
     dist_init(world, local, "nccl")
-    k_cap, every, tol, m, budget = 300, 10, 1e-6, 20, 1.0
+    k_cap, every, tol, m, budget = args.batched_cap, args.batched_every, args.batched_tol, 20, 1.0
+    prec = ovs.F64 if args.batched_prec == "f64" else ovs.MIXED
+    skip = not args.batched_every_check
     specs = synth.batched_instances(args.instances)
     gs, xs, ys = [], [], []
     t0 = time.perf_counter()
@@ -558,19 +567,21 @@ def run_batched(args, world, rank, local, steps, warmup):
     t_setup = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=ovs.MIXED, check_every=every, tol=tol, want_info=False)
+        ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=prec, check_every=every, tol=tol, want_info=False,
+                               skip_ahead=skip)
     torch.cuda.synchronize()
     barrier(world)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=ovs.MIXED, check_every=every, tol=tol, want_info=False)
+        ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=prec, check_every=every, tol=tol, want_info=False,
+                               skip_ahead=skip)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     ms_max = max_over_ranks(e0.elapsed_time(e1), world, torch.device("cuda", local))
-    st, info = ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=ovs.MIXED, check_every=every, tol=tol)
+    st, info = ovs.sign_apply_batched(gs, xs, ys, k_cap, prec=prec, check_every=every, tol=tol, skip_ahead=skip)
     total = sum(sp["nrhs"] for sp in specs)
     ks = np.array([i["k_used"] for i in info])
     # FP64 single-RHS reference of one right-hand side per lattice size, at
@@ -578,7 +589,7 @@ def run_batched(args, world, rank, local, steps, warmup):
     errs, off = {}, 0
     for sp, g, x, y in zip(specs, gs, xs, ys):
         key = "x".join(map(str, sp["dims"]))
-        if key not in errs:
+        if prec == ovs.MIXED and key not in errs:
             k0 = int(info[off]["k_used"])
             y64 = torch.empty_like(x[:1])
             ovs.sign_apply(g, x[:1].contiguous(), y64, max(k0, 1), prec=ovs.F64)
@@ -588,9 +599,12 @@ def run_batched(args, world, rank, local, steps, warmup):
         "metric": "batched sgn(H_w(mu))x applications/s, multi-instance recipe, per-vector stop",
         "value": round(job_value(total, steps, world, ms_max), 3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": warmup, "ms_per_step": round(ms_max / steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == ovs.F64 else "f32", "data": "synthetic",
         "config": {"workload": f"{len(specs)} instances (4^4/6^4/8^4 cycle, mu 0.1/0.2/0.3), "
-                               f"{total} RHS, m={m} each, stop at {tol} every {every} steps, cap k={k_cap}",
+                               f"{total} RHS, m={m} each, stop at {tol} on multiples of {every} steps "
+                               f"({'every interval' if not skip else 'skip-ahead schedule'}), cap k={k_cap}",
+                   "checks": "every interval" if not skip else "skip-ahead",
                    "instances": len(specs), "rhs_total": total, "setup_budget_s_each": budget,
                    "setup_seconds_total": round(t_setup, 1), "parallelism": "replicas"},
         "k_used": {"min": int(ks.min()), "median": float(np.median(ks)), "max": int(ks.max()),

@@ -211,7 +211,8 @@ typedef struct {
                             (zero-padded) is below tol; V is orthonormal,
                             so this is the change of its Krylov part */
     int32_t prec;        /* OVS_F64 or OVS_MIXED */
-    int32_t flags;       /* 0 or OVS_APPLY_HARMONIC (other bits: EINVAL) */
+    int32_t flags;       /* 0, OVS_APPLY_HARMONIC or OVS_APPLY_SKIP_AHEAD
+                            (other bits: EINVAL) */
     double tol;          /* tolerance for check_every > 0 */
 } ovs_apply_opts;
 
@@ -221,6 +222,21 @@ typedef struct {
  * harmonic Ritz values of H_w on the Krylov space); y = ... + beta V_k
  * sgn(H^_k) e_1. Needs check_every = 0 and no Schur deflation. */
 #define OVS_APPLY_HARMONIC 1
+
+/* opts->flags: skip-ahead schedule of the convergence checks (needs
+ * check_every > 0; not a method of the paper, which fixes k). The checks
+ * stay on multiples of check_every, up to J = check_every floor((k_max-1) /
+ * check_every). A check whose previous check lies check_every steps back
+ * gives a one-interval estimate. After two of them, e0 at j0 and e1 < e0 at
+ * j1, the estimate is extrapolated geometrically: it reaches tol after
+ * n = log(tol/e1) / (log(e1/e0)/(j1-j0)) more steps, and the checks (and
+ * their sign computations) are skipped up to P = check_every floor((j1 + n)
+ * / check_every) - check_every (at most J - check_every). The check at P
+ * only stores its coefficients, unless its estimate (over the longer
+ * interval) is already below tol; the check at P + check_every gives the
+ * next one-interval estimate. Every stop still needs an estimate below tol;
+ * est_err is the last estimate formed. */
+#define OVS_APPLY_SKIP_AHEAD 2
 
 /* Per right-hand-side report. */
 typedef struct {

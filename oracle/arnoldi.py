@@ -19,7 +19,21 @@ Readings where the paper is silent:
 * stopping by convergence (batched form; the paper fixes k instead): every
   `every` (even) steps form c_j = beta sgn(H_j) e_1 and stop at the first j
   with ||c_j - c_(j-every)|| / ||c_j|| < tol (c padded with zeros); as V is
-  orthonormal this is the relative change of beta V_j sgn(H_j) e_1.
+  orthonormal this is the relative change of beta V_j sgn(H_j) e_1;
+* skip-ahead check schedule (optional; fewer sign computations while the
+  estimate is far from tol): the checks fall on multiples of `every`, the
+  last one allowed for extrapolation at J = every floor((k_max - 1)/every).
+  A check whose previous check lies exactly `every` steps back gives a
+  one-interval estimate. After two such estimates e0 (at j0) and e1 (at j1)
+  with e1 < e0, the estimate is extrapolated geometrically: it reaches tol
+  after n = log(tol/e1) / (log(e1/e0)/(j1 - j0)) more steps, and the checks
+  are skipped up to P = every floor((j1 + n)/every) - every (at most
+  J - every). The check at P stores c_P (its estimate spans more than one
+  interval; it still stops the iteration if below tol) and the check at
+  P + every, the last multiple of `every` before the extrapolated stop,
+  gives the next one-interval estimate. On a geometric convergence this
+  stops at the same j as checking every `every` steps; a convergence that
+  speeds up can stop later. Every stop still needs an estimate below tol.
 """
 
 import numpy as np
@@ -96,23 +110,42 @@ def arnoldi_sign(matvec, x, k, harmonic=False, **newton_kw):
     return y, dict(k_used=k_used, beta=beta, newton_iters=it, coeff=coeff, H=h)
 
 
-def arnoldi_sign_adaptive(matvec, x, k_max, every, tol, **newton_kw):
-    """Eq. yproj3 with k chosen by the convergence estimate above.
+def arnoldi_sign_adaptive(matvec, x, k_max, every, tol, skip_ahead=False, **newton_kw):
+    """Eq. yproj3 with k chosen by the convergence estimate above (with
+    ``skip_ahead``, on the skip-ahead schedule).
 
-    Returns (y, info) with info = dict(k_used, est, beta, coeff).
+    Returns (y, info) with info = dict(k_used, est, beta, coeff, checks), where
+    checks lists the j at which sgn(H_j) was formed.
     """
     v, h, beta, k_run = arnoldi(matvec, x, k_max)
+    cap = every * ((k_max - 1) // every)
     c_prev = np.zeros(0, dtype=np.complex128)
+    j_prev = 0
     est = 0.0
-    for j in range(every, k_run + 1, every):
+    hist = []  # (j, one-interval estimate)
+    checks = []
+    j = every
+    while j <= k_run:
         s, _ = roberts_sign(h[:j, :j], **newton_kw)
+        checks.append(j)
         c = beta * s[:, 0]
         prev = np.zeros(j, dtype=np.complex128)
         prev[: c_prev.shape[0]] = c_prev
         est = np.linalg.norm(c - prev) / np.linalg.norm(c)
-        c_prev = c
         if est < tol:
-            return v[:, :j] @ c, dict(k_used=j, est=est, beta=beta, coeff=c)
+            return v[:, :j] @ c, dict(k_used=j, est=est, beta=beta, coeff=c, checks=checks)
+        nxt = j + every
+        if skip_ahead and j_prev > 0 and j - j_prev == every:
+            hist.append((j, est))
+            if len(hist) >= 2 and hist[-1][1] < hist[-2][1]:
+                (j0, e0), (j1, e1) = hist[-2], hist[-1]
+                n = np.log(tol / e1) / (np.log(e1 / e0) / (j1 - j0))
+                t = j1 + n
+                p = cap - every if t >= cap else every * int(np.floor(t / every)) - every
+                nxt = max(nxt, p)
+        c_prev, j_prev = c, j
+        j = nxt
     y, info = arnoldi_sign(matvec, x, k_run, **newton_kw)
     info["est"] = est
+    info["checks"] = checks
     return y, info

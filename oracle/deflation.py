@@ -59,20 +59,21 @@ def lr_sign_apply(matvec, x, r, l, lam, k, **newton_kw):
     return y_defl + y_kr, info
 
 
-def lr_sign_apply_adaptive(matvec, x, r, l, lam, k_max, every, tol, **newton_kw):
+def lr_sign_apply_adaptive(matvec, x, r, l, lam, k_max, every, tol, skip_ahead=False, **newton_kw):
     """LR deflation (Eq. fAxLRArn) whose Krylov part stops by the convergence
     estimate of ``arnoldi_sign_adaptive`` (the batched form's per-vector stop,
-    not in the paper): the deflated part is exact, so the estimate is taken
+    not in the paper; ``skip_ahead`` selects its skip-ahead check schedule):
+    the deflated part is exact, so the estimate is taken
     on the Krylov coefficients of x_ominus. Returns (y, info) as
     ``lr_sign_apply``, with info["k_used"] the step of the stop."""
     x = np.asarray(x, dtype=np.complex128)
     if r is None or r.shape[1] == 0:
-        y, info = arnoldi_sign_adaptive(matvec, x, k_max, every, tol, **newton_kw)
+        y, info = arnoldi_sign_adaptive(matvec, x, k_max, every, tol, skip_ahead, **newton_kw)
         info["c"] = np.zeros(0, np.complex128)
         return y, info
     l_bi = biorthonormalise(r, l)
     c, x_om = lr_split(x, r, l_bi)
-    y_kr, info = arnoldi_sign_adaptive(matvec, x_om, k_max, every, tol, **newton_kw)
+    y_kr, info = arnoldi_sign_adaptive(matvec, x_om, k_max, every, tol, skip_ahead, **newton_kw)
     info["c"] = c
     return r @ (sgn_re(lam) * c) + y_kr, info
 

@@ -36,6 +36,7 @@ EXPORTS = [
 ]
 PROF_CLASSES = ["matvec", "dots", "update", "small", "newton", "layout", "proj"]
 APPLY_HARMONIC = 1
+APPLY_SKIP_AHEAD = 2
 SCHEME = {0: "none", 1: "lr", 2: "schur"}
 
 
@@ -307,9 +308,13 @@ def deflate_restore(g, path):
     _check(load().ovs_deflate_restore(g.handle, os.fsencode(path)))
 
 
-def _apply(fn, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info, harmonic):
+def _flags(harmonic=False, skip_ahead=False):
+    return (APPLY_HARMONIC if harmonic else 0) | (APPLY_SKIP_AHEAD if skip_ahead else 0)
+
+
+def _apply(fn, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info, harmonic, skip_ahead=False):
     nrhs = x.shape[0] if nrhs is None else nrhs
-    opts = ApplyOpts(int(k_max), int(check_every), int(prec), APPLY_HARMONIC if harmonic else 0, float(tol))
+    opts = ApplyOpts(int(k_max), int(check_every), int(prec), _flags(harmonic, skip_ahead), float(tol))
     if want_info:
         info = (ApplyInfo * nrhs)()
         st = _check(fn(g.handle, _ptr(x), _ptr(y), int(nrhs), ctypes.byref(opts), info, _stream(stream)))
@@ -318,9 +323,11 @@ def _apply(fn, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info, 
 
 
 def sign_apply(g, x, y, k_max, prec=MIXED, nrhs=None, check_every=0, tol=0.0, stream=None, want_info=True,
-               harmonic=False):
-    """y = sgn(H_w(mu)) x. Returns (status, [info dicts]) if want_info, else status."""
-    return _apply(load().ovs_sign_apply, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info, harmonic)
+               harmonic=False, skip_ahead=False):
+    """y = sgn(H_w(mu)) x. Returns (status, [info dicts]) if want_info, else status.
+    skip_ahead: the skip-ahead schedule of the convergence checks."""
+    return _apply(load().ovs_sign_apply, g, x, y, k_max, prec, nrhs, check_every, tol, stream, want_info, harmonic,
+                  skip_ahead)
 
 
 def overlap_apply(g, x, y, k_max, prec=MIXED, nrhs=None, check_every=0, tol=0.0, stream=None, want_info=True,
@@ -357,7 +364,8 @@ def get_krylov(g, rhs):
     return V, H.T.copy()
 
 
-def sign_apply_batched(gauges, xs, ys, k_max, prec=MIXED, check_every=0, tol=0.0, stream=None, want_info=True):
+def sign_apply_batched(gauges, xs, ys, k_max, prec=MIXED, check_every=0, tol=0.0, stream=None, want_info=True,
+                       skip_ahead=False):
     """Batched form over several handles: y_i = sgn(H_w(mu_i)) x_i for each
     instance i (xs[i], ys[i] of shape [nrhs_i, N_i])."""
     n = len(gauges)
@@ -365,7 +373,7 @@ def sign_apply_batched(gauges, xs, ys, k_max, prec=MIXED, check_every=0, tol=0.0
     xp = (ctypes.c_void_p * n)(*[_ptr(x).value for x in xs])
     yp = (ctypes.c_void_p * n)(*[_ptr(y).value for y in ys])
     nr = (ctypes.c_int32 * n)(*[int(x.shape[0]) for x in xs])
-    opts = ApplyOpts(int(k_max), int(check_every), int(prec), 0, float(tol))
+    opts = ApplyOpts(int(k_max), int(check_every), int(prec), _flags(skip_ahead=skip_ahead), float(tol))
     lib = load()
     if want_info:
         total = sum(int(x.shape[0]) for x in xs)

@@ -223,6 +223,8 @@ static void free_kry(KryWork& k) {
     dfree(k.ccheck[0]);
     dfree(k.ccheck[1]);
     dfree(k.est);
+    dfree(k.due);
+    dfree(k.cstate);
     dfree(k.partial);
     dfree(k.norm_part);
     dfree(k.beta);
@@ -340,6 +342,8 @@ static int ensure_kry(ovs_gauge_s* g, int nrhs, int kmax, int tprec) {
     CK(dalloc(&k.ccheck[0], sizeof(double2) * (size_t)km * n));
     CK(dalloc(&k.ccheck[1], sizeof(double2) * (size_t)km * n));
     CK(dalloc(&k.est, sizeof(double) * n));
+    CK(dalloc(&k.due, sizeof(int) * n));
+    CK(dalloc(&k.cstate, sizeof(CheckState) * n));
     CK(cudaMemset(k.err, 0, sizeof(int)));
     CK(dalloc(&k.partial, sizeof(double2) * (size_t)nb * jc * n));
     CK(dalloc(&k.norm_part, sizeof(double) * (size_t)nb * n));
@@ -820,9 +824,12 @@ static int check_apply(ovs_gauge_s* g, int nrhs, const ovs_apply_opts* opts) {
     const int every = opts->check_every;
     if (every < 0 || (every % 2) != 0) return fail(OVS_EINVAL, "check_every must be 0 or a positive even number");
     if (every > 0 && !(opts->tol > 0.0)) return fail(OVS_EINVAL, "check_every > 0 needs tol > 0");
-    if ((opts->flags & ~OVS_APPLY_HARMONIC) != 0) return fail(OVS_EINVAL, "unknown bits in opts->flags");
+    if ((opts->flags & ~(OVS_APPLY_HARMONIC | OVS_APPLY_SKIP_AHEAD)) != 0)
+        return fail(OVS_EINVAL, "unknown bits in opts->flags");
     const bool harmonic = (opts->flags & OVS_APPLY_HARMONIC) != 0;
     if (harmonic && every > 0) return fail(OVS_EINVAL, "OVS_APPLY_HARMONIC needs check_every = 0");
+    if ((opts->flags & OVS_APPLY_SKIP_AHEAD) != 0 && every == 0)
+        return fail(OVS_EINVAL, "OVS_APPLY_SKIP_AHEAD needs check_every > 0");
     if (g->scheme == DEFL_SCHUR && (every > 0 || harmonic))
         return fail(OVS_EINVAL, "Schur deflation supports fixed-k applications without OVS_APPLY_HARMONIC");
     if (g->scheme == DEFL_SCHUR && !schur_coeff_fits(k)) return fail(OVS_EINVAL, "k_max too large for Schur deflation");
@@ -943,8 +950,13 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
     }
     CK(cudaMemsetAsync(kw.active, 0xff, sizeof(int) * nrhs, st));  // every rhs starts active (-1 != 0)
     CK(cudaMemsetAsync(kw.est, 0, sizeof(double) * nrhs, st));
-    int cbuf = 0;
-    if (every > 0) CK(cudaMemsetAsync(kw.ccheck[0], 0, sizeof(double2) * kmax * nrhs, st));
+    CheckState* cstate = static_cast<CheckState*>(kw.cstate);
+    const bool skip = (opts->flags & OVS_APPLY_SKIP_AHEAD) != 0;
+    const int check_cap = every > 0 ? every * ((k - 1) / every) : 0;
+    if (every > 0) {  // ccheck[0]: the coefficients of the last check (none yet: zero)
+        CK(cudaMemsetAsync(kw.ccheck[0], 0, sizeof(double2) * kmax * nrhs, st));
+        KL(OVS_PROF_SMALL, 32.0 * nrhs, launch_check_init(cstate, every, nrhs, st));
+    }
 
     // Arnoldi (Sec. 4, Eq. Arnoldi; Sec. 5.3 Eq. LRArnoldi) with classical
     // Gram-Schmidt applied twice, the second pass of step j-1 done in the
@@ -993,18 +1005,19 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
                launch_schur_xcol(kw.X, x_rhs, m, j, kw.htmp, kw.jcap, kw.inv_beta, kw.active, nrhs, st));
         KL(OVS_PROF_SMALL, 16.0 * ((double)j * j / 2 + 2.0 * j) * nrhs,
            launch_arnoldi_column(kw.htmp, kw.jcap, j, kw.H, h_rhs, ldh, kw.inv_beta, kw.dcoef, kw.active, nrhs, st));
-        // A7 (batched form): every `every` steps, the sign of the complete
-        // H_j of each active right-hand side; stop it once successive
-        // coefficient vectors agree to tol (V orthonormal, so this is the
-        // change of its Krylov part).
+        // A7 (batched form): at the checks (every `every` steps, or on the
+        // skip-ahead schedule) the sign of the complete H_j of each active
+        // right-hand side that is due; stop it once successive coefficient
+        // vectors agree to tol (V orthonormal, so this is the change of its
+        // Krylov part).
         if (every > 0 && j > 0 && j % every == 0) {
+            KL(OVS_PROF_SMALL, 12.0 * nrhs, launch_check_due(kw.active, cstate, j, kw.due, nrhs, st));
             KL(OVS_PROF_NEWTON, 16.0 * (double)j * j * nrhs,
-               launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.ccheck[1 - cbuf], kmax, kw.newton, (int)kmax,
-                             nrhs, kw.iters, kw.status, st, kw.active, j));
-            KL(OVS_PROF_SMALL, 32.0 * j * nrhs,
-               launch_conv_check(kw.ccheck[1 - cbuf], kw.ccheck[cbuf], kmax, j, opts->tol, kw.active, kw.k_used,
-                                 kw.est, nrhs, st));
-            cbuf = 1 - cbuf;
+               launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.ccheck[1], kmax, kw.newton, (int)kmax, nrhs,
+                             kw.iters, kw.status, st, kw.due, j));
+            KL(OVS_PROF_SMALL, 48.0 * j * nrhs,
+               launch_conv_check(kw.ccheck[1], kw.ccheck[0], kmax, j, opts->tol, kw.active, kw.k_used, kw.est,
+                                 kw.due, cstate, every, check_cap, skip, nrhs, st));
         }
         if (tma)
             KL(OVS_PROF_UPDATE, (double)N * sz_of(tp) * nrhs * (j + 4.0),
@@ -1039,10 +1052,14 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
     if (opts->flags & OVS_APPLY_HARMONIC)
         KL(OVS_PROF_SMALL, 16.0 * (double)k * (k + 1) * nrhs,
            launch_harmonic(kw.H, h_rhs, ldh, kw.k_used, kw.newton, (int)kmax, nrhs, st));
-    // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v; Sec. 5.2 step v for H_k)
+    // K3: beta sgn(H_k) e_1 (Sec. 5.3 step v; Sec. 5.2 step v for H_k); a
+    // right-hand side stopped by a convergence check has it already
+    if (every > 0)
+        KL(OVS_PROF_SMALL, 32.0 * k * nrhs,
+           launch_check_final(cstate, kw.ccheck[0], kw.coeff, kmax, kw.k_used, kw.due, nrhs, st));
     KL(OVS_PROF_NEWTON, 16.0 * (double)k * k * nrhs,
        launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.coeff, kmax, kw.newton, (int)kmax, nrhs, kw.iters,
-                     kw.status, st));
+                     kw.status, st, every > 0 ? kw.due : nullptr));
     if (schur) {
         // Schur coefficients sgn(T) c + beta Y e_1 (App. A), then y = S cS
         KL(OVS_PROF_SMALL, 16.0 * ((double)m * k * 4 + (double)k * k) * nrhs,

@@ -525,7 +525,12 @@ bool setup_log() {
     return v != nullptr && v[0] == '1';
 }
 
-int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadline_s, SideResult& res) {
+// start: a device block of p complex128 vectors (internal layout) to start
+// from, or null for a seeded random block. want: eigenvalues that must each
+// have a Ritz pair at tol (relative distance <= 1e-6) before the side counts
+// as converged, or null.
+int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadline_s, SideResult& res,
+             const double2* start = nullptr, const std::vector<std::complex<double>>* want = nullptr) {
     const auto t_start = std::chrono::steady_clock::now();
     const bool log = setup_log();
     const int p = c.p;
@@ -535,7 +540,10 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
     int rc = spectral_bound(c, mu, &b);
     if (rc) return rc;
     const double hnorm = std::sqrt(b);
-    ECK(launch_random_fill(c.Q, (long long)p * N, seed, c.st));
+    if (start)
+        ECK(cudaMemcpyAsync(c.Q, start, sizeof(double2) * (size_t)p * N, cudaMemcpyDeviceToDevice, c.st));
+    else
+        ECK(launch_random_fill(c.Q, (long long)p * N, seed, c.st));
     rc = svqb(c);
     if (rc) return rc;
     // complex64 phase: filter, orthonormalisation and Rayleigh-Ritz all in
@@ -578,6 +586,17 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
         for (int i = 0; i < p; ++i) rr[i] = res.resid[i] / hnorm;
         std::nth_element(rr.begin(), rr.begin() + (m - 1), rr.end());
         return rr[m - 1];
+    };
+    // every wanted eigenvalue has a Ritz pair at tol next to it
+    auto partners_ok = [&]() {
+        if (!want) return true;
+        for (const auto& w : *want) {
+            bool found = false;
+            for (int i = 0; i < p && !found; ++i)
+                found = res.resid[i] / hnorm <= tol && std::abs(res.theta[i] - w) <= 1e-6 * std::abs(w);
+            if (!found) return false;
+        }
+        return true;
     };
     auto count_at_tol = [&]() {
         int n = 0;
@@ -703,7 +722,7 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
             rmax = mth_resid();
         }
         res.iters = it + 1;
-        if (rmax <= tol && have64) {
+        if (rmax <= tol && have64 && partners_ok()) {
             res.converged = true;
             break;
         }
@@ -728,7 +747,7 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
         ECK(launch_convert(PREC_F64, c.F[0], c.Q, (long long)p * N, c.st));
         rc = certify_pairs(res.iters);
         if (rc) return rc;
-        res.converged = mth_resid() <= tol;
+        res.converged = mth_resid() <= tol && partners_ok();
     }
     // hand the Ritz vectors (now in Q) to the caller, sorted by |theta|
     std::vector<std::complex<double>> th(p);
@@ -860,8 +879,24 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
     double2* Rblk = nullptr;
     if (cudaMalloc((void**)&Rblk, blk) != cudaSuccess) return lib_fail(OVS_ENOMEM, "deflate_setup: right block");
     cudaMemcpy(Rblk, c.Q, blk, cudaMemcpyDeviceToDevice);
-    // left eigenvectors: right eigenvectors of H_w(-mu), eigenvalues conj(lambda)
-    rc = run_side(c, m, tol, -g->mu, 54321, side_s, left);
+    // left eigenvectors: right eigenvectors of H_w(-mu), eigenvalues
+    // conj(lambda). The iteration starts from the right side's Ritz vectors
+    // (H_w(-mu) = H_w(mu)^H differs from H_w(mu) only in the temporal hops,
+    // so left and right eigenvectors are close), and it runs until every
+    // right pair that will be installed (at tol, smallest |Re lambda|) has a
+    // partner at tol: two independent runs would converge on different
+    // fringes of the wanted set and leave pairs unmatched.
+    std::vector<std::complex<double>> want;
+    {
+        std::vector<int> at;
+        for (int i = 0; i < p; ++i)
+            if (right.resid[i] <= tol) at.push_back(i);
+        std::stable_sort(at.begin(), at.end(), [&](int x, int y) {
+            return std::fabs(right.theta[x].real()) < std::fabs(right.theta[y].real());
+        });
+        for (int i = 0; i < (int)at.size() && i < m; ++i) want.push_back(std::conj(right.theta[at[i]]));
+    }
+    rc = run_side(c, m, tol, -g->mu, 54321, side_s, left, Rblk, &want);
     if (rc) {
         cudaFree(Rblk);
         SETUP_FAIL(rc);

@@ -29,6 +29,8 @@ struct KryWork {  // Krylov basis and small matrices
     int* err = nullptr;          // device error word (OVS_ETIMEOUT from bounded waits)
     void* ccheck[2] = {nullptr, nullptr};  // [nrhs][kmax] coefficient vectors of successive checks
     double* est = nullptr;                 // [nrhs] last convergence estimate
+    int* due = nullptr;                    // [nrhs] checked at this step (A7)
+    void* cstate = nullptr;                // [nrhs] CheckState: the check schedule (A7)
     void* partial = nullptr;     // [nrhs][nblk][jcap] complex128
     double* norm_part = nullptr; // [nrhs][nblk]
     double* beta = nullptr;

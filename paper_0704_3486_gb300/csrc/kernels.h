@@ -189,8 +189,26 @@ cudaError_t launch_gmres_col(const void* red1, const void* red2, long long red_s
                              cudaStream_t st);
 cudaError_t launch_gmres_backsub(const void* R, const void* gv, int jj, int restart, void* y, int nrhs,
                                  cudaStream_t st);
-// est[r] = ||cnew_r - cold_r|| / ||cnew_r||; below tol: active[r] = 0, k_used[r] = n
-cudaError_t launch_conv_check(const void* cnew, const void* cold, long long stride, int n, double tol, int* active,
-                              int* k_used, double* est, int nrhs, cudaStream_t st);
+// A7 convergence checks: per right-hand side state of the check schedule
+// (jl: j of the coefficients kept for comparison; (j0, e0), (j1, e1): the
+// last two one-interval estimates; next: j of the next check)
+struct CheckState {
+    int jl, j0, j1, next;
+    double e0, e1;
+};
+cudaError_t launch_check_init(CheckState* cs, int every, int nrhs, cudaStream_t st);
+// after the last step: due[r] = 0 for a right-hand side stopped by a check
+// (its coefficients, kept in cold, copied to coeff), else 1
+cudaError_t launch_check_final(const CheckState* cs, const void* cold, void* coeff, long long stride,
+                               const int* k_used, int* due, int nrhs, cudaStream_t st);
+// due[r] = active[r] and cs[r].next == j
+cudaError_t launch_check_due(const int* active, const CheckState* cs, int j, int* due, int nrhs, cudaStream_t st);
+// for the due right-hand sides: the estimate ||cnew - cold|| / ||cnew|| over
+// the first n entries, the stop (active = 0, k_used = n) below tol, else cold
+// = cnew and the next check (skip: the skip-ahead schedule; cap: the last
+// check j the schedule may aim at)
+cudaError_t launch_conv_check(const void* cnew, void* cold, long long stride, int n, double tol, int* active,
+                              int* k_used, double* est, const int* due, CheckState* cs, int every, int cap,
+                              bool skip, int nrhs, cudaStream_t st);
 
 }  // namespace ovs

@@ -519,16 +519,21 @@ __global__ void __launch_bounds__(NTC)
     }
 }
 
-// Convergence estimate of the batched form (one block per right-hand side):
-// est = ||c_new - c_old|| / ||c_new|| over the coefficient vectors of two
-// checks (zero beyond their sizes); below tol the right-hand side stops with
-// k_used = n.
-__global__ void k_conv_check(const double2* __restrict__ cnew, const double2* __restrict__ cold, long long stride,
-                             int n, double tol, int* __restrict__ active, int* __restrict__ k_used,
-                             double* __restrict__ est) {
+// Convergence estimate of the batched form (one block per right-hand side
+// that is due): est = ||c_new - c_old|| / ||c_new|| over the coefficient
+// vectors of two checks (zero beyond their sizes); below tol the right-hand
+// side stops with k_used = n. Otherwise c_new becomes c_old and the next
+// check is scheduled: `every` steps on, or with the skip-ahead schedule
+// (two one-interval estimates e0 > e1 at j0 < j1) at P = every floor((j1 + n')
+// / every) - every, n' = log(tol/e1) / (log(e1/e0)/(j1 - j0)) the steps the
+// geometric extrapolation needs to reach tol, P at most cap - every.
+__global__ void k_conv_check(const double2* __restrict__ cnew, double2* __restrict__ cold, long long stride, int n,
+                             double tol, int* __restrict__ active, int* __restrict__ k_used,
+                             double* __restrict__ est, const int* __restrict__ due, CheckState* __restrict__ cs,
+                             int every, int cap, int skip) {
     __shared__ double sh[33];
     const int r = blockIdx.x;
-    if (active[r] == 0) return;
+    if (due[r] == 0) return;
     double d2 = 0.0, c2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const double2 a = cnew[r * stride + i], b = cold[r * stride + i];
@@ -536,20 +541,83 @@ __global__ void k_conv_check(const double2* __restrict__ cnew, const double2* __
         c2 += a.x * a.x + a.y * a.y;
     }
     d2 = blk_sum(d2, sh);
-    c2 = blk_sum(c2, sh);
+    c2 = blk_sum(c2, sh);  // every read of cold is done: it may be overwritten
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cold[r * stride + i] = cnew[r * stride + i];
     if (threadIdx.x == 0) {
         const double e = c2 > 0.0 ? sqrt(d2 / c2) : 0.0;
         est[r] = e;
         if (e < tol) {
             active[r] = 0;
             k_used[r] = n;
+            cs[r].next = -1;  // stopped here: cold holds beta sgn(H_n) e_1
+            return;
         }
+        CheckState s = cs[r];
+        int nxt = n + every;
+        if (skip && s.jl > 0 && n - s.jl == every) {
+            s.j0 = s.j1;
+            s.e0 = s.e1;
+            s.j1 = n;
+            s.e1 = e;
+            if (s.j0 > 0 && s.e1 < s.e0) {
+                const double steps = log(tol / s.e1) / (log(s.e1 / s.e0) / (double)(s.j1 - s.j0));
+                const double t = (double)s.j1 + steps;
+                const int pn = t >= (double)cap ? cap - every : every * (int)floor(t / (double)every) - every;
+                nxt = max(nxt, pn);
+            }
+        }
+        s.jl = n;
+        s.next = nxt;
+        cs[r] = s;
     }
 }
 
-cudaError_t launch_conv_check(const void* cnew, const void* cold, long long stride, int n, double tol, int* active,
-                              int* k_used, double* est, int nrhs, cudaStream_t st) {
-    k_conv_check<<<nrhs, 256, 0, st>>>((const double2*)cnew, (const double2*)cold, stride, n, tol, active, k_used, est);
+__global__ void k_check_init(CheckState* __restrict__ cs, int every, int nrhs) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nrhs) cs[r] = CheckState{0, 0, 0, every, 0.0, 0.0};
+}
+
+__global__ void k_check_due(const int* __restrict__ active, const CheckState* __restrict__ cs, int j,
+                            int* __restrict__ due, int nrhs) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nrhs) due[r] = (active[r] != 0 && cs[r].next == j) ? 1 : 0;
+}
+
+// After the last step: a right-hand side stopped by a check already has its
+// coefficients beta sgn(H_k_used) e_1 (in cold): copy them to coeff and
+// leave it out of the final sign computation (due = 0); the others are due.
+__global__ void k_check_final(const CheckState* __restrict__ cs, const double2* __restrict__ cold,
+                              double2* __restrict__ coeff, long long stride, const int* __restrict__ k_used,
+                              int* __restrict__ due) {
+    const int r = blockIdx.x;
+    const bool stopped = cs[r].next == -1;
+    if (threadIdx.x == 0) due[r] = stopped ? 0 : 1;
+    if (!stopped) return;
+    const int n = k_used[r];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) coeff[r * stride + i] = cold[r * stride + i];
+}
+
+cudaError_t launch_check_final(const CheckState* cs, const void* cold, void* coeff, long long stride,
+                               const int* k_used, int* due, int nrhs, cudaStream_t st) {
+    k_check_final<<<nrhs, 256, 0, st>>>(cs, (const double2*)cold, (double2*)coeff, stride, k_used, due);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_init(CheckState* cs, int every, int nrhs, cudaStream_t st) {
+    k_check_init<<<(nrhs + 127) / 128, 128, 0, st>>>(cs, every, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_due(const int* active, const CheckState* cs, int j, int* due, int nrhs, cudaStream_t st) {
+    k_check_due<<<(nrhs + 127) / 128, 128, 0, st>>>(active, cs, j, due, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_check(const void* cnew, void* cold, long long stride, int n, double tol, int* active,
+                              int* k_used, double* est, const int* due, CheckState* cs, int every, int cap,
+                              bool skip, int nrhs, cudaStream_t st) {
+    k_conv_check<<<nrhs, 256, 0, st>>>((const double2*)cnew, (double2*)cold, stride, n, tol, active, k_used, est,
+                                       due, cs, every, cap, skip ? 1 : 0);
     return cudaGetLastError();
 }
 

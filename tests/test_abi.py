@@ -109,3 +109,5 @@ def test_solve_struct_layouts_and_flags():
     text = open(os.path.join(ROOT, "include", "ovsign.h")).read()
     m = re.search(r"#define\s+OVS_APPLY_HARMONIC\s+(\d+)", text)
     assert m and int(m.group(1)) == ovs.APPLY_HARMONIC
+    m = re.search(r"#define\s+OVS_APPLY_SKIP_AHEAD\s+(\d+)", text)
+    assert m and int(m.group(1)) == ovs.APPLY_SKIP_AHEAD

@@ -50,6 +50,40 @@ def test_convergence_stop_matches_oracle(gpu):
     g.destroy()
 
 
+@pytest.mark.parametrize("tol", [1e-3, 1e-5])
+def test_skip_ahead_schedule_matches_oracle(gpu, tol):
+    """OVS_APPLY_SKIP_AHEAD: the device schedule stops every right-hand side
+    at the oracle's j (its skip-ahead schedule, decided from the same
+    estimates), single and batched, with the fixed-k result there."""
+    specs = [((4, 4, 4, 4), 3, 0.5, 0.3, 3), ((4, 4, 4, 4), 4, 0.6, 0.2, 2)]
+    inst = []
+    for dims, seed, eps, mu, nrhs in specs:
+        links = synth.gauge_links(dims, seed, eps)
+        h = lattice.hw_operator(links, dims, mu, MW)
+        g = gpu.create_gauge_from_links(dims, links, gpu.F64)
+        gpu.set_mu(g, mu, MW)
+        x = synth.gaussian_vectors(h.shape[0], nrhs, seed + 40)
+        inst.append((g, h, x))
+    xs = [torch.from_numpy(x).cuda() for _, _, x in inst]
+    ys = [torch.empty_like(x) for x in xs]
+    st, binfo = gpu.sign_apply_batched([i[0] for i in inst], xs, ys, 300, prec=gpu.F64, check_every=10, tol=tol,
+                                       skip_ahead=True)
+    off = 0
+    for (g, h, x), xd, yd in zip(inst, xs, ys):
+        y1 = torch.empty_like(xd)
+        st, info = gpu.sign_apply(g, xd, y1, 300, prec=gpu.F64, check_every=10, tol=tol, skip_ahead=True)
+        assert torch.equal(y1, yd)
+        y = yd.cpu().numpy()
+        for r in range(x.shape[0]):
+            ref, oinfo = arnoldi.arnoldi_sign_adaptive(lambda q: h @ q, x[r], 300, 10, tol, skip_ahead=True)
+            assert info[r]["k_used"] == oinfo["k_used"] == binfo[off + r]["k_used"]
+            assert abs(info[r]["est_err"] - oinfo["est"]) <= 1e-9 * oinfo["est"]
+            assert rel(y[r], ref) < 1e-12
+        off += x.shape[0]
+    for g, _, _ in inst:
+        g.destroy()
+
+
 def test_convergence_not_reached_is_flagged(gpu):
     dims, mu = (4, 4, 4, 4), 0.3
     g = gpu.create_gauge(dims, 1, 0.5, gpu.F64)

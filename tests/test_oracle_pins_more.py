@@ -351,3 +351,52 @@ def test_gmres_pin_catches_planted_mistake():
     bad = _mutant("overlap", "rhs[0] = beta", "rhs[0] = -beta")
     x, info = bad.gmres(lambda q: a @ q, b, 10, 1e-12, 5)
     assert not info["converged"] or rel(x, np.linalg.solve(a, b)) > 1e-3
+
+
+# ------------------------------- skip-ahead check schedule (batched form)
+def _skip_problem():
+    dims = (4, 4, 4, 4)
+    u = synth.gauge_links(dims, 3, 0.5)
+    h = lattice.hw_operator(u, dims, 0.3, MW)
+    return h, synth.gaussian_vectors(h.shape[0], 1, 2)[0]
+
+
+def _check_schedule(mod, h, x, tol):
+    """Invariants of the skip-ahead schedule against checking every interval
+    on the same problem (whose convergence slows down, so the extrapolation
+    never overshoots): the same stop, fewer sign computations, all on
+    multiples of the interval, and the result of the fixed-k method at the
+    stop, where the change against the previous check is below tol."""
+    mv = lambda q: h @ q
+    y, info = mod.arnoldi_sign_adaptive(mv, x, 300, 10, tol, skip_ahead=True)
+    _, fixed = arnoldi.arnoldi_sign_adaptive(mv, x, 300, 10, tol)
+    ch = info["checks"]
+    assert ch[:3] == [10, 20, 30] and all(j % 10 == 0 for j in ch) and ch == sorted(set(ch))
+    assert len(ch) < len(fixed["checks"])
+    assert info["k_used"] == fixed["k_used"]
+    y_fix, at = arnoldi.arnoldi_sign(mv, x, info["k_used"])
+    assert np.linalg.norm(y - y_fix) < 1e-13 * np.linalg.norm(y_fix)
+    if info["k_used"] < 300:
+        _, before = arnoldi.arnoldi_sign(mv, x, ch[-2])
+        c = at["coeff"]
+        cb = np.zeros_like(c)
+        cb[: before["coeff"].shape[0]] = before["coeff"]
+        assert np.linalg.norm(c - cb) < tol * np.linalg.norm(c)
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-5, 1e-8])
+def test_skip_ahead_schedule(tol):
+    h, x = _skip_problem()
+    _check_schedule(arnoldi, h, x, tol)
+
+
+@pytest.mark.parametrize("old,new", [("np.log(e1 / e0)", "np.log(e0 / e1)"),
+                                     ("j - j_prev == every", "j - j_prev >= every")])
+def test_skip_ahead_pin_catches_planted_mistake(old, new):
+    """A flipped rate (no skipping at all) and rates taken from estimates
+    over more than one interval (late stops) each break an invariant."""
+    h, x = _skip_problem()
+    bad = _mutant("arnoldi", old, new)
+    with pytest.raises(AssertionError):
+        for tol in (1e-3, 1e-5):
+            _check_schedule(bad, h, x, tol)
