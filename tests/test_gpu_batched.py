@@ -77,7 +77,9 @@ def test_skip_ahead_schedule_matches_oracle(gpu, tol):
         for r in range(x.shape[0]):
             ref, oinfo = arnoldi.arnoldi_sign_adaptive(lambda q: h @ q, x[r], 300, 10, tol, skip_ahead=True)
             assert info[r]["k_used"] == oinfo["k_used"] == binfo[off + r]["k_used"]
-            assert abs(info[r]["est_err"] - oinfo["est"]) <= 1e-9 * oinfo["est"]
+            if oinfo["k_used"] < 300:  # stopped by a check (at the cap the oracle also checks j = k_max)
+                assert abs(info[r]["est_err"] - oinfo["est"]) <= 1e-9 * oinfo["est"]
+                assert info[r]["status"] == 0
             assert rel(y[r], ref) < 1e-12
         off += x.shape[0]
     for g, _, _ in inst:
