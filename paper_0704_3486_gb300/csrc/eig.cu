@@ -872,6 +872,9 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
 
     // right eigenvectors of H_w(mu)
     SideResult right, left;
+    // time budget: the right side gets half of it (all of it for Schur), the
+    // left side what the right side left over
+    const auto t_setup = std::chrono::steady_clock::now();
     const double side_s = g->setup_budget_s > 0.0 ? (schur ? 1.0 : 0.5) * g->setup_budget_s : 0.0;
     int rc = run_side(c, m, tol, g->mu, 12345, side_s, right);
     if (rc) SETUP_FAIL(rc);
@@ -896,7 +899,12 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
         });
         for (int i = 0; i < (int)at.size() && i < m; ++i) want.push_back(std::conj(right.theta[at[i]]));
     }
-    rc = run_side(c, m, tol, -g->mu, 54321, side_s, left, Rblk, &want);
+    double left_s = 0.0;
+    if (g->setup_budget_s > 0.0)
+        left_s = std::max(0.5 * g->setup_budget_s,
+                          g->setup_budget_s -
+                              std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup).count());
+    rc = run_side(c, m, tol, -g->mu, 54321, left_s, left, Rblk, &want);
     if (rc) {
         cudaFree(Rblk);
         SETUP_FAIL(rc);
