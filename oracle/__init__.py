@@ -21,7 +21,8 @@ Modules and the passages they follow:
                    twice (Sec. 4, Eqs. Arnoldi, HVAV) and the approximation
                    f(A)x ~ beta V_k f(H_k) e_1 (Sec. 4, Eq. yproj3), at a
                    fixed k or stopped by the change of the coefficient
-                   vector between checks (the batched form's criterion).
+                   vector between checks (the batched form's criterion),
+                   the checks every interval or on the skip-ahead schedule.
 * ``deflation`` -- LR deflation (Sec. 5.3, Eqs. Rev, Lev, xdec, fAxLR, fARLx,
                    LRArnoldi, fAxLRArn), also with the adaptive stop, and
                    critical eigenpairs (Sec. 6).
