@@ -605,13 +605,27 @@ __global__ void k_sign_scale(const double2* __restrict__ c, const double* __rest
 // (the LR projection L^+ x, the Schur projections S^H z of every Arnoldi
 // step): partial[(r*nblk + b)*pstride + i] = sum over the units of chunk b
 // of S_i^H z_r, i < m, r < nrhs. A block takes one chunk of units and stages
-// it KD units at a time, every S_i and every z_r, in shared memory (unit-
-// major, so that the threads of a warp read consecutive vectors); each
-// thread accumulates a tile of 4 basis vectors x 2 right-hand sides: FP32
-// over one staged tile (2 KD complex terms), FP64 across tiles. Each
-// element of the basis is read from memory once per call, not once per
-// right-hand side.
+// it KD units at a time, every S_i and every z_r, in shared memory by
+// asynchronous 16-byte copies (cp.async), two stages deep: the copies of
+// tile t+1 are in flight while tile t is multiplied, so a block keeps
+// (m + nrhs) KD 16-byte units in flight without registers. Stage layout
+// vector-major with a row pitch of KD+1 units: the copies write consecutive
+// units, and the threads of a quarter warp, reading 8 consecutive vectors
+// at one unit, fall on 8 distinct 4-bank groups. Each thread accumulates a
+// tile of 4 basis vectors x 2 right-hand sides: FP32 over one staged tile
+// (2 KD complex terms), FP64 across tiles. Each element of the basis is
+// read from memory once per call, not once per right-hand side.
 constexpr int KD = 32;
+constexpr int KP = KD + 1;  // row pitch of a staged vector, in units
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;  // 0: nothing is read, the 16 bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __global__ void __launch_bounds__(BT) k_shared_dots(const float4* __restrict__ S, long long svec, int m,
                                                     const float4* __restrict__ Z, long long zstride, int nrhs,
@@ -619,8 +633,8 @@ __global__ void __launch_bounds__(BT) k_shared_dots(const float4* __restrict__ S
                                                     double2* __restrict__ partial, int pstride,
                                                     const int* __restrict__ active) {
     extern __shared__ float4 sd_smem[];
-    float4* sS = sd_smem;                   // [KD][m]
-    float4* sZ = sd_smem + (size_t)KD * m;  // [KD][nrhs]
+    const int rows = m + nrhs;  // staged vectors: S_0 .. S_(m-1), then z_0 .. z_(nrhs-1)
+    const size_t stage = (size_t)rows * KP;
     const int b = blockIdx.x, tid = threadIdx.x;
     const long long u0 = (long long)b * chunk;
     const long long u1 = min(u0 + chunk, nunits);
@@ -633,17 +647,30 @@ __global__ void __launch_bounds__(BT) k_shared_dots(const float4* __restrict__ S
 #pragma unroll
         for (int c = 0; c < 2; ++c) acc[a][c][0] = acc[a][c][1] = 0.0;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (long long t0 = u0; t0 < u1; t0 += KD) {
-        const int cnt = (int)min((long long)KD, u1 - t0);
-        for (int idx = tid; idx < m * KD; idx += BT) {
-            const int i = idx / KD, u = idx - i * KD;
-            sS[(size_t)u * m + i] = (u < cnt) ? __ldg(S + (size_t)i * svec + t0 + u) : zero;
+    // copies of the tile at unit t0 into stage buffer st (zero beyond u1)
+    auto issue = [&](long long t0, int st) {
+        float4* dst = sd_smem + st * stage;
+        for (int idx = tid; idx < rows * KD; idx += BT) {
+            const int row = idx / KD, u = idx - row * KD;
+            const bool valid = t0 + u < u1;
+            const float4* src = row < m ? S + (size_t)row * svec : Z + (size_t)(row - m) * zstride;
+            cp_async16(dst + (size_t)row * KP + u, valid ? src + t0 + u : S, valid);
         }
-        for (int idx = tid; idx < nrhs * KD; idx += BT) {
-            const int r = idx / KD, u = idx - r * KD;
-            sZ[(size_t)u * nrhs + r] = (u < cnt) ? __ldg(Z + (size_t)r * zstride + t0 + u) : zero;
+        cp_async_commit();
+    };
+    const long long ntile = (u1 - u0 + KD - 1) / KD;
+    if (ntile > 0) issue(u0, 0);
+    for (long long t = 0; t < ntile; ++t) {
+        if (t + 1 < ntile) {
+            issue(u0 + (t + 1) * KD, (int)((t + 1) & 1));
+            cp_async_wait<1>();  // tile t has landed (tile t+1 may still be in flight)
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const float4* sS = sd_smem + (t & 1) * stage;
+        const float4* sZ = sS + (size_t)m * KP;
+        const int cnt = (int)min((long long)KD, u1 - (u0 + t * KD));
         if (work) {
             float a32[4][2][2];
 #pragma unroll
@@ -655,12 +682,12 @@ __global__ void __launch_bounds__(BT) k_shared_dots(const float4* __restrict__ S
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int i = ti + q * itiles;
-                    sv[q] = (i < m) ? sS[(size_t)u * m + i] : zero;
+                    sv[q] = (i < m) ? sS[(size_t)i * KP + u] : zero;
                 }
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int r = tr + q * rtiles;
-                    zv[q] = (r < nrhs) ? sZ[(size_t)u * nrhs + r] : zero;
+                    zv[q] = (r < nrhs) ? sZ[(size_t)r * KP + u] : zero;
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
@@ -687,7 +714,7 @@ __global__ void __launch_bounds__(BT) k_shared_dots(const float4* __restrict__ S
                     acc[a][c][1] += (double)a32[a][c][1];
                 }
         }
-        __syncthreads();
+        __syncthreads();  // stage (t & 1) is refilled by the copies issued in the next iteration
     }
     if (!work) return;
 #pragma unroll
@@ -701,14 +728,18 @@ __global__ void __launch_bounds__(BT) k_shared_dots(const float4* __restrict__ S
         }
 }
 
+static size_t shared_dots_smem(int m, int nrhs) { return 2 * (size_t)(m + nrhs) * KP * sizeof(float4); }
+
 // Blocks of the shared-basis dots for nunits within the partial slots
-// available; 0 when the tile does not fit (the register sweep k_gdots
-// serves then).
+// available: as many per SM as their two stages fit (at most 4); 0 when the
+// tile does not fit (the register sweep k_gdots serves then).
 int shared_dots_blocks(int m, int nrhs, long long nunits, int num_sms, int max_blocks) {
     const int itiles = (m + 3) / 4, rtiles = (nrhs + 1) / 2;
     if (m < 1 || nrhs < 1 || (long long)itiles * rtiles > BT) return 0;
-    if ((size_t)(m + nrhs) * KD * sizeof(float4) > 200 * 1024) return 0;
-    long long want = 2LL * num_sms;
+    const size_t smem = shared_dots_smem(m, nrhs);
+    if (smem > 200 * 1024) return 0;
+    const long long per_sm = std::max<long long>(1, std::min<long long>(4, (long long)(220 * 1024) / (long long)smem));
+    long long want = per_sm * num_sms;
     want = std::min<long long>(want, std::max<long long>(1, nunits / KD));
     want = std::min<long long>(want, max_blocks);
     return want < 1 ? 0 : (int)want;
@@ -717,7 +748,7 @@ int shared_dots_blocks(int m, int nrhs, long long nunits, int num_sms, int max_b
 cudaError_t launch_shared_dots(const void* S, long long svec, int m, const void* Z, long long zstride, int nrhs,
                                long long nunits, int nblk, void* partial, int pstride, const int* active,
                                cudaStream_t st) {
-    const size_t smem = (size_t)(m + nrhs) * KD * sizeof(float4);
+    const size_t smem = shared_dots_smem(m, nrhs);
     cudaError_t e = ensure_dyn_smem((const void*)k_shared_dots, 200 * 1024);
     if (e != cudaSuccess) return e;
     long long chunk = (nunits + nblk - 1) / nblk;

@@ -526,9 +526,10 @@ bool setup_log() {
 }
 
 // start: a device block of p complex128 vectors (internal layout) to start
-// from, or null for a seeded random block. want: eigenvalues that must each
-// have a Ritz pair at tol (relative distance <= 1e-6) before the side counts
-// as converged, or null.
+// from, or null for a seeded random block. want: eigenvalues in order of
+// preference, of which m must find partners, Ritz pairs at tol at relative
+// distance <= 1e-6 (matched greedily, nearest first, as the final selection
+// does), before the side counts as converged; or null.
 int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadline_s, SideResult& res,
              const double2* start = nullptr, const std::vector<std::complex<double>>* want = nullptr) {
     const auto t_start = std::chrono::steady_clock::now();
@@ -587,16 +588,25 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
         std::nth_element(rr.begin(), rr.begin() + (m - 1), rr.end());
         return rr[m - 1];
     };
-    // every wanted eigenvalue has a Ritz pair at tol next to it
+    // m of the wanted eigenvalues have partners: the final selection will
+    // find m matched pairs
     auto partners_ok = [&]() {
         if (!want) return true;
+        std::vector<char> taken(p, 0);
+        int matched = 0;
         for (const auto& w : *want) {
-            bool found = false;
-            for (int i = 0; i < p && !found; ++i)
-                found = res.resid[i] / hnorm <= tol && std::abs(res.theta[i] - w) <= 1e-6 * std::abs(w);
-            if (!found) return false;
+            int best = -1;
+            double bd = 1e300;
+            for (int i = 0; i < p; ++i) {
+                if (taken[i] || !(res.resid[i] / hnorm <= tol)) continue;
+                const double d = std::abs(res.theta[i] - w);
+                if (d < bd) { bd = d; best = i; }
+            }
+            if (best < 0 || bd > 1e-6 * std::abs(w)) continue;
+            taken[best] = 1;
+            if (++matched == m) return true;
         }
-        return true;
+        return false;
     };
     auto count_at_tol = [&]() {
         int n = 0;
@@ -885,10 +895,11 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
     // left eigenvectors: right eigenvectors of H_w(-mu), eigenvalues
     // conj(lambda). The iteration starts from the right side's Ritz vectors
     // (H_w(-mu) = H_w(mu)^H differs from H_w(mu) only in the temporal hops,
-    // so left and right eigenvectors are close), and it runs until every
-    // right pair that will be installed (at tol, smallest |Re lambda|) has a
-    // partner at tol: two independent runs would converge on different
-    // fringes of the wanted set and leave pairs unmatched.
+    // so left and right eigenvectors are close), and it runs until m of the
+    // right pairs at tol (in the order of the selection below: smallest
+    // |Re lambda| first) have partners at tol: two independent runs would
+    // converge on different fringes of the wanted set and leave pairs
+    // unmatched.
     std::vector<std::complex<double>> want;
     {
         std::vector<int> at;
@@ -897,7 +908,7 @@ int eig_setup(ovs_gauge_s* g, int m, double tol, double* eig_out, bool schur) {
         std::stable_sort(at.begin(), at.end(), [&](int x, int y) {
             return std::fabs(right.theta[x].real()) < std::fabs(right.theta[y].real());
         });
-        for (int i = 0; i < (int)at.size() && i < m; ++i) want.push_back(std::conj(right.theta[at[i]]));
+        for (int i : at) want.push_back(std::conj(right.theta[i]));
     }
     double left_s = 0.0;
     if (g->setup_budget_s > 0.0)
