@@ -242,7 +242,8 @@ class CpuSample:
         import synth
         from oracle import deflation
 
-        w, h, ks, k, m = self.w, self.h, self.ks, self.w["k"], self.w["m"]
+        w, h, k, m = self.w, self.h, self.w["k"], self.w["m"]
+        ks = max(3, min(self.ks, k))  # sampled steps: at most the workload's k, 3 for the fit
         x = synth.gaussian_vectors(w["N"], 1, w["src_seed"] + seed_offset)[0]
         stamps = []
 
