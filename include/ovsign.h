@@ -138,12 +138,15 @@ int ovs_matvec_noalloc(ovs_gauge_t g, int32_t op, const void* x, void* y, int32_
  * H_w(mu)^2 (the paper's choice), right vectors R with H R = R Lambda, left
  * vectors as right eigenvectors of H_w(mu)^+ = H_w(-mu) (gamma5-
  * hermiticity), biorthonormalised so that L^+ R = I. The m kept are those
- * of smallest |Re lambda| among the converged ones. tol: relative residual
+ * of smallest |Re lambda| among the converged right pairs that have a
+ * converged left partner (eigenvalue conj(lambda) within relative distance
+ * 1e-6); the left iteration starts from the right one's final block and
+ * runs until m such pairs exist. tol: relative residual
  * ||H r - lambda r|| / ||H|| asked of each pair (e.g. 1e-10). eig_out, if
  * not NULL, receives the m eigenvalues as 2m doubles (re, im), sorted by
- * |Re lambda|. Synchronises the device. Errors: EINVAL, ESTATE, EEIG (the
- * pairs did not reach tol within the iteration budget; the basis is still
- * installed and eig_out filled), ENOMEM, ECUDA. */
+ * |Re lambda|. Synchronises the device. Errors: EINVAL, ESTATE, EEIG (fewer
+ * than m matched pairs reached tol within the iteration budget; the nearest
+ * pairs are installed instead and eig_out filled), ENOMEM, ECUDA. */
 int ovs_deflate_setup(ovs_gauge_t g, int32_t m, double tol, double* eig_out);
 
 /* Statistics of the last ovs_deflate_setup on this handle: iterations of
