@@ -83,7 +83,7 @@ def wilson_dirac(links, dims, mu, m_w, convention="minus_forward"):
     one = np.eye(4, dtype=np.complex128)
     sign_fwd = -1.0 if convention == "minus_forward" else +1.0
     if convention not in ("minus_forward", "paper"):
-        raise ValueError("convention must be 'baseline' or 'paper'")
+        raise ValueError("convention must be 'minus_forward' or 'paper'")
     sites = np.arange(v)
     rows_all, cols_all, vals_all = [], [], []
     # diagonal delta_{n,m}
@@ -133,7 +133,7 @@ def wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention="minus_forward
     lx, ly, lz, lt = dims
     sites = np.asarray(sites, dtype=np.int64)
     if convention not in ("minus_forward", "paper"):
-        raise ValueError("convention must be 'baseline' or 'paper'")
+        raise ValueError("convention must be 'minus_forward' or 'paper'")
     sign_fwd = -1.0 if convention == "minus_forward" else +1.0
     kappa = kappa_of(m_w)
     gam = gamma_matrices()
@@ -150,7 +150,7 @@ def wilson_dirac_sites(links, dims, mu, m_w, x, sites, convention="minus_forward
             c[nu] = raw % dims[nu]
             nb = ((c[3] * lz + c[2]) * ly + c[1]) * lx + c[0]
             bc = np.where(wrapped & (nu == 3), -1.0, 1.0)
-            if step > 0:  # psi(s + nu) through U_nu(s), (1 - gamma_nu) in the baseline convention
+            if step > 0:  # psi(s + nu) through U_nu(s), (1 - gamma_nu) in the minus_forward convention
                 proj = one + sign_fwd * gam[nu]
                 u = links[sites, nu]
                 w = tfac
