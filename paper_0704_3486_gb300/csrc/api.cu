@@ -1059,7 +1059,7 @@ static int sign_apply_core(ovs_gauge_s* g, const void* xd, void* yd, int nrhs, c
            launch_check_final(cstate, kw.ccheck[0], kw.coeff, kmax, kw.k_used, kw.due, nrhs, st));
     KL(OVS_PROF_NEWTON, 16.0 * (double)k * k * nrhs,
        launch_newton(kw.H, h_rhs, ldh, kw.k_used, kw.beta, kw.coeff, kmax, kw.newton, (int)kmax, nrhs, kw.iters,
-                     kw.status, st, every > 0 ? kw.due : nullptr));
+                     kw.status, st, every > 0 ? kw.due : nullptr, 0, k));  // k_used[r] <= k
     if (schur) {
         // Schur coefficients sgn(T) c + beta Y e_1 (App. A), then y = S cS
         KL(OVS_PROF_SMALL, 16.0 * ((double)m * k * 4 + (double)k * k) * nrhs,

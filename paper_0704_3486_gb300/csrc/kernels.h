@@ -157,7 +157,8 @@ cudaError_t launch_sign_scale(const void* c, const double* sgn, int m, int nrhs,
 // sides with active[r] == 0 are skipped when active != nullptr.
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
-                          int* status, cudaStream_t st, const int* active = nullptr, int n_fixed = 0);
+                          int* status, cudaStream_t st, const int* active = nullptr, int n_fixed = 0,
+                          int k_bound = 0);
 // harmonic variant: H_r[:, k-1] += |h_(k+1,k)|^2 H_k^-H e_k (k = k_used[r]);
 // work as for launch_newton (used as scratch before it)
 cudaError_t launch_harmonic(void* H, long long h_rhs_stride, int ldh, const int* k_used, void* work, int kmax,

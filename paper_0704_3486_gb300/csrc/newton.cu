@@ -781,10 +781,16 @@ static int pick_cluster(int kmax, int nrhs) {
 
 cudaError_t launch_newton(const void* H, long long h_rhs_stride, int ldh, const int* k_used, const double* beta,
                           void* coeff, long long coeff_stride, void* work, int kmax, int nrhs, int* iters,
-                          int* status, cudaStream_t st, const int* active, int n_fixed) {
-    // matrices of a known order (the convergence checks) need shared memory
-    // for that order only, so they can use the cluster form below kmax
-    const int kc = (n_fixed > 0 && n_fixed < kmax) ? n_fixed : kmax;
+                          int* status, cudaStream_t st, const int* active, int n_fixed, int k_bound) {
+    // matrices of a known order (the convergence checks), or of orders
+    // bounded by the call's Krylov dimension, need shared memory for that
+    // order only, so they can use the cluster form below kmax (the work
+    // space may have been sized by an earlier call with a larger k)
+    int kc = kmax;
+    if (n_fixed > 0 && n_fixed < kmax)
+        kc = n_fixed;
+    else if (n_fixed <= 0 && k_bound > 0 && k_bound < kmax)
+        kc = k_bound;
     const int ncl = pick_cluster(kc, nrhs);
     if (ncl > 0) {
         cudaLaunchConfig_t cfg = {};
