@@ -527,9 +527,9 @@ bool setup_log() {
 
 // start: a device block of p complex128 vectors (internal layout) to start
 // from, or null for a seeded random block. want: eigenvalues in order of
-// preference, of which m must find partners, Ritz pairs at tol at relative
-// distance <= 1e-6 (matched greedily, nearest first, as the final selection
-// does), before the side counts as converged; or null.
+// preference, of which m (all, if fewer) must find partners, Ritz pairs at
+// tol at relative distance <= 1e-6 (matched greedily, nearest first, as the
+// final selection does), before the side counts as converged; or null.
 int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadline_s, SideResult& res,
              const double2* start = nullptr, const std::vector<std::complex<double>>* want = nullptr) {
     const auto t_start = std::chrono::steady_clock::now();
@@ -588,10 +588,12 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
         std::nth_element(rr.begin(), rr.begin() + (m - 1), rr.end());
         return rr[m - 1];
     };
-    // m of the wanted eigenvalues have partners: the final selection will
-    // find m matched pairs
+    // m of the wanted eigenvalues (all of them, if fewer) have partners: the
+    // final selection will find as many matched pairs as it can
     auto partners_ok = [&]() {
         if (!want) return true;
+        const int need = std::min<int>(m, (int)want->size());
+        if (need == 0) return true;
         std::vector<char> taken(p, 0);
         int matched = 0;
         for (const auto& w : *want) {
@@ -604,7 +606,7 @@ int run_side(Ctx& c, int m, double tol, double mu, uint64_t seed, double deadlin
             }
             if (best < 0 || bd > 1e-6 * std::abs(w)) continue;
             taken[best] = 1;
-            if (++matched == m) return true;
+            if (++matched == need) return true;
         }
         return false;
     };
